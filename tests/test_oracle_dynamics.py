@@ -1,0 +1,154 @@
+"""Pins of the oracle's integrator, stopping, window dynamics and cloning.
+
+* energy conservation with stopping off: the KDK error scales as dt^2;
+* electronic stopping alone: the drag ODE M dv/dt = -gamma v has the closed
+  form range M (v0 - v_stop) / gamma;
+* rare-event enhancement: weights are exact powers of two and sum to the
+  number of primaries; the weighted range distribution with splitting equals
+  the one without (the paper's "same statistics" statement, Sec. 2);
+* the time step grows as the ion slows (Fig. dt_E, qualitatively).
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_0810_4737_gb300.workloads import workload, B11, AS75
+
+
+def _cluster(a=5.431, m=2):
+    fcc = np.array([[0, 0, 0], [0, 2, 2], [2, 0, 2], [2, 2, 0]], dtype=float) / 4.0
+    basis = np.vstack([fcc, fcc + 0.25])
+    return np.vstack([(basis + [i, j, k]) * a for i in range(m) for j in range(m) for k in range(m)])
+
+
+@pytest.mark.parametrize("tt", ["none", "tersoff"])
+def test_energy_conservation_is_second_order(O, tt):
+    w = workload("as10kev_si_300k_tersoff", tt=tt, lattice="explicit", energy=500.0, e_stop=0.0)
+    p = O.params(w)
+    rng = np.random.default_rng(1)
+    X = _cluster() + rng.normal(scale=0.05, size=(64, 3))
+    V = np.zeros_like(X)
+    sp = np.zeros(64, dtype=np.int32)
+    x0 = np.array([2.5, 3.1, -1.0])
+    v0 = np.array([0.3, 0.2, 1.0])
+    v0 *= np.sqrt(2 * 500.0 / AS75["M"]) / np.linalg.norm(v0)
+    T = 1.2  # tau
+    errs = []
+    for dt in (4e-4, 2e-4):
+        n = int(round(T / dt))
+        *_, E = O.md_explicit(p, x0, v0, X, V, sp, nsteps=n, dt_fixed=dt, energies=True)
+        errs.append(np.max(np.abs(E - E[0])))
+    ratio = errs[0] / errs[1]
+    assert errs[1] < 2e-3 * 500.0
+    assert 3.3 < ratio < 4.8, (errs, ratio)
+
+
+def test_drag_range_closed_form(O):
+    """Nuclear forces off (no atoms): the ion slows as v(t) = v0 exp(-gamma t/M)
+    and travels M (v0 - v_stop)/gamma before E < E_stop."""
+    w = workload("b1kev_si_0k_zbl", e_stop=5.0)
+    p = O.params(w)
+    gam = O.gamma_ls(p)
+    M = B11["M"]
+    v0 = np.sqrt(2 * 1000.0 / M)
+    vs = np.sqrt(2 * 5.0 / M)
+    xi, vi, *_ = O.md_explicit(p, [0.0, 0.0, 0.0], [0.0, 0.0, v0], np.zeros((0, 3)), np.zeros((0, 3)),
+                               np.zeros(0, dtype=np.int32), nsteps=10_000_000)
+    expect = M * (v0 - vs) / gamma_check(gam)
+    # stop is detected at step granularity: overshoot < one step
+    assert abs(xi[2] - expect) < 1e-3 * expect + 0.05
+    # Lindhard-Scharff magnitude for B in Si: gamma is independent of M1
+    p2 = O.params(workload("b1kev_si_0k_zbl", ion={"Z": 5.0, "M": 22.0}))
+    assert abs(O.gamma_ls(p2) / gam - 1) < 1e-14
+
+
+def gamma_check(g):
+    assert g > 0
+    return g
+
+
+def test_drag_scales_with_local_density(O):
+    """With s_loc = 1 the drag follows the local density; in vacuum (no
+    atoms) it is (1 - s_loc) times the uniform value."""
+    p1 = O.params(workload("b1kev_si_0k_zbl", s_loc=1.0))
+    p0 = O.params(workload("b1kev_si_0k_zbl", s_loc=0.0))
+    M = B11["M"]
+    v0 = np.sqrt(2 * 1000.0 / M)
+    res = []
+    for p in (p0, p1):
+        xi, vi, *_ = O.md_explicit(p, [0.0, 0.0, 0.0], [0.0, 0.0, v0], np.zeros((0, 3)), np.zeros((0, 3)),
+                                   np.zeros(0, dtype=np.int32), nsteps=2000, dt_fixed=1e-3)
+        res.append(vi[2])
+    assert res[0] < v0 - 1e-3
+    assert res[1] == v0
+
+
+def test_weights_are_conserved_with_cloning(O):
+    w = workload("b1kev_si_0k_zbl", sigma=0.076, energy=2000.0,
+                 thresholds=[15.0, 25.0, 40.0, 60.0, 90.0, 130.0])
+    p = O.params(w)
+    r = O.run(p, 48, seed=5, threads=8)
+    rec = r["records"]
+    wts = np.ldexp(1.0, -rec["level"].astype(int))
+    assert np.sum(wts) == 48.0                       # exact in FP64
+    total = r["hist"].sum() + r["under"] + r["over"] + r["back"] + r["w_trunc"]
+    assert total == 48.0
+    assert r["clones"] == len(rec) - 48 > 48
+    # every clone sits deeper than the cloning depth that created it
+    thr = np.array(w["thresholds"])
+    for lvl in range(1, 7):
+        z = rec["z"][(rec["level"] == lvl) & (rec["status"] == 1)]
+        # a track at level L crossed d_L at some time, it may have come back
+        assert len(z) == 0 or np.max(z) > thr[lvl - 1]
+    # one primary per lineage, the primary keeps its id
+    assert len(np.unique(rec["primary"])) == 48
+
+
+def _wks(a, wa, b, wb):
+    """Weighted two-sample KS statistic and p-value with n_eff = (sum w)^2 / sum w^2."""
+    xs = np.concatenate([a, b])
+    order = np.argsort(xs, kind="mergesort")
+    ca = np.cumsum(np.concatenate([wa / wa.sum(), np.zeros(len(b))])[order])
+    cb = np.cumsum(np.concatenate([np.zeros(len(a)), wb / wb.sum()])[order])
+    D = np.max(np.abs(ca - cb))
+    na = wa.sum() ** 2 / np.sum(wa ** 2)
+    nb = wb.sum() ** 2 / np.sum(wb ** 2)
+    ne = na * nb / (na + nb)
+    return D, stats.kstwo.sf(D, int(round(ne)))
+
+
+def test_splitting_preserves_the_range_distribution(O):
+    base = workload("b1kev_si_0k_zbl", sigma=0.076, rot=(0.0, 45.0))
+    plain = O.run(O.params(base), 1500, seed=21, threads=8)
+    enh = O.run(O.params(dict(base, thresholds=[60.0, 100.0, 150.0, 220.0])), 1500, seed=22, threads=8)
+    ra, rb = plain["records"], enh["records"]
+    ka, kb = ra["status"] == 1, rb["status"] == 1
+    za, zb = ra["z"][ka], rb["z"][kb]
+    wa = np.ones(ka.sum())
+    wb = np.ldexp(1.0, -rb["level"][kb].astype(int))
+    D, pval = _wks(za, wa, zb, wb)
+    assert pval > 0.01, (D, pval)
+    ma, mb = np.average(za, weights=wa), np.average(zb, weights=wb)
+    assert abs(ma / mb - 1) < 0.05
+    # the enhanced run resolves the deep tail with many more tracks
+    deep = 220.0
+    assert np.sum(zb > deep) > 3 * np.sum(za > deep)
+
+
+def test_time_step_grows_as_the_ion_slows(O):
+    w = workload("b1kev_si_0k_zbl", energy=20000.0, sigma=0.076)
+    p = O.params(w)
+    tr, anc = O.trace(p, 0, 3, 200000)
+    dt = tr[:, 7]
+    E = 0.5 * B11["M"] * np.sum(tr[:, 4:7] ** 2, axis=1)
+    assert dt.max() / dt.min() > 10.0
+    # dt is the step-length cap at high energy and the 0.1 fs cap at low energy
+    assert abs(dt.max() - 0.1 / O.TAU_FS) < 1e-12
+    # the step length never exceeds 0.05 A for the ion (dt uses the speed at
+    # the start of the step; fast recoils can only shorten it)
+    vprev = np.linalg.norm(tr[:-1, 4:7], axis=1)
+    assert np.all(dt[1:] * vprev <= 0.05 * (1 + 1e-9))
+    hi = E[:-1] > 1e4
+    assert np.mean(np.abs(dt[1:][hi] * vprev[hi] - 0.05) < 1e-9) > 0.9
+    # anchors move by at most one cell per axis per step
+    assert np.max(np.abs(np.diff(anc, axis=0))) <= 1

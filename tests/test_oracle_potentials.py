@@ -1,0 +1,267 @@
+"""Pins of the oracle's interatomic potentials.
+
+ZBL: the screening function sums to one at the origin; analytic forces
+agree with central differences; the two-body scattering angle produced by
+the oracle's integrator equals the classical deflection integral, which is
+itself pinned to the Rutherford closed form.  Tersoff Si(C): the published
+cohesive energy, lattice constant and bulk modulus; the b = 1 dimer limit;
+zero force on a perfect lattice; brute-force finite-difference forces.
+Buckingham/fluorite: symmetry and finite differences.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from conftest import GOLDEN
+from paper_0810_4737_gb300.workloads import workload, SI, B11, AS75, CE, O16
+
+E2 = 14.399645  # eV A
+
+
+def test_zbl_screening_is_one_at_origin(O):
+    for Z1, Z2 in [(5, 14), (33, 14), (14, 14), (18, 8)]:
+        r = 1e-7
+        V, _ = O.zbl(Z1, Z2, r)
+        assert abs(V * r / (Z1 * Z2 * E2) - 1.0) < 1e-5
+        # and decays faster than bare Coulomb
+        V5, _ = O.zbl(Z1, Z2, 5.0)
+        assert V5 < 0.02 * Z1 * Z2 * E2 / 5.0
+
+
+def test_ion_pair_force_matches_finite_difference(O):
+    w = workload("b1kev_si_0k_zbl", spline_c=[0.05, -0.03, 0.02, 0.04, -0.05, 0.01])
+    p = O.params(w)
+    for r in np.linspace(0.05, 4.99, 211):
+        h = 1e-6 * r
+        Up, _ = O.ion_pair(p, 14.0, r + h)
+        Um, _ = O.ion_pair(p, 14.0, r - h)
+        _, dU = O.ion_pair(p, 14.0, r)
+        fd = (Up - Um) / (2 * h)
+        assert abs(fd - dU) <= 1e-7 * max(abs(dU), 1e-3), (r, fd, dU)
+
+
+def test_taper_is_c2(O):
+    rt, rc = 4.5, 5.0
+    S, dS = O.taper(rt, rt, rc)
+    assert S == 1.0 and dS == 0.0
+    S, dS = O.taper(rc, rt, rc)
+    assert S == 0.0 and dS == 0.0
+    h = 1e-5
+    for r0 in (rt, rc):
+        d2 = (O.taper(r0 + h, rt, rc)[0] - 2 * O.taper(r0, rt, rc)[0] + O.taper(r0 - h, rt, rc)[0]) / h ** 2
+        assert abs(d2) < 1e-3
+    # monotone
+    rs = np.linspace(rt, rc, 101)
+    Ss = [O.taper(r, rt, rc)[0] for r in rs]
+    assert np.all(np.diff(Ss) <= 0)
+
+
+def deflection_angle(V, Ec, b):
+    """Classical centre-of-mass deflection angle
+    theta = pi - 2 b int_{rmin}^inf dr / (r^2 sqrt(1 - V/Ec - b^2/r^2)).
+    With u = rmin/r the integral is (1/rmin) int_0^1 du / sqrt(F(rmin/u));
+    u = 1 - t^2 removes the inverse-square-root end-point singularity."""
+    from scipy.optimize import brentq
+    F = lambda r: 1.0 - V(r) / Ec - (b / r) ** 2
+    lo, hi = 1e-6, max(b, 1e-3)
+    while F(hi) <= 0:
+        hi *= 2
+    rmin = brentq(F, lo, hi, xtol=1e-15, rtol=1e-15)
+    while F(rmin) < 0.0:   # F > 0 for every r > rmin
+        rmin = np.nextafter(rmin, np.inf)
+
+    def h(t):
+        if t <= 1e-7:
+            t = 1e-7
+        return 2.0 * t / np.sqrt(F(rmin / (1.0 - t * t)))
+
+    val, _ = integrate.quad(h, 0.0, 1.0, epsabs=1e-13, epsrel=1e-13, limit=500)
+    return np.pi - 2.0 * b / rmin * val
+
+
+def test_deflection_integral_reduces_to_rutherford():
+    k = 5 * 14 * E2
+    for Ec, b in [(100.0, 0.1), (1000.0, 0.05), (1000.0, 0.5), (50.0, 2.0)]:
+        th = deflection_angle(lambda r: k / r, Ec, b)
+        assert abs(th - 2 * np.arctan(k / (2 * Ec * b))) < 1e-8
+
+
+@pytest.mark.parametrize("ion,E,b", [(B11, 1000.0, 0.2), (B11, 1000.0, 1.0), (AS75, 10000.0, 0.3),
+                                     (AS75, 2000.0, 1.5)])
+def test_two_body_md_matches_deflection_integral(O, ion, E, b):
+    w = workload("b1kev_si_0k_zbl", ion=ion, lattice="explicit", energy=E)
+    p = O.params(w)
+    M1, M2 = ion["M"], SI["M"]
+    v0 = np.sqrt(2 * E / M1)
+    rc = w["rc"]
+    z0 = -np.sqrt(rc ** 2 - b ** 2) - 1e-6
+    dt = 0.0015 / v0
+    xi, vi, xa, va, k, _ = O.md_explicit(p, [b, 0.0, z0], [0.0, 0.0, v0], [[0.0, 0.0, 0.0]],
+                                         [[0.0, 0.0, 0.0]], [0], nsteps=200000, dt_fixed=dt,
+                                         stop_sep=rc + 1e-3)
+    assert k < 200000
+    vrel0 = np.array([0.0, 0.0, v0])
+    vrel1 = vi - va[0]
+    th_md = np.arccos(np.dot(vrel0, vrel1) / (np.linalg.norm(vrel0) * np.linalg.norm(vrel1)))
+    mu = M1 * M2 / (M1 + M2)
+    Ec = 0.5 * mu * v0 ** 2
+
+    def V(r):
+        return O.ion_pair(p, SI["Z"], r)[0] if r < rc else 0.0
+
+    th = deflection_angle(V, Ec, b)
+    assert abs(th_md - th) < 1e-4, (th_md, th)
+    # elastic: |v_rel| conserved
+    assert abs(np.linalg.norm(vrel1) / v0 - 1) < 1e-6
+
+
+def _tersoff_params(O, a=5.432):
+    return O.params(workload("as10kev_si_300k_tersoff", a=a, sigma=0.0))
+
+
+def _diamond_block(a, m):
+    fcc = np.array([[0, 0, 0], [0, 2, 2], [2, 0, 2], [2, 2, 0]], dtype=float) / 4.0
+    basis = np.vstack([fcc, fcc + 0.25])
+    pts = [(basis + [i, j, k]) * a for i in range(m) for j in range(m) for k in range(m)]
+    return np.vstack(pts)
+
+
+def _bulk_energy_per_atom(O, p, a):
+    """Energy per atom of bulk diamond.  A cubic block of m^3 cells of a
+    short-ranged potential has E(m) = e_b 8 m^3 + s 6 m^2 + l 12 m + c (bulk,
+    faces, edges, corners) once its faces no longer see each other; four
+    block sizes determine e_b exactly."""
+    rows, y = [], []
+    for m in (4, 5, 6, 7):
+        X = _diamond_block(a, m)
+        y.append(O.forces(p, [1e4, 1e4, 1e4], X, np.zeros(len(X), dtype=np.int32), with_ion=False)[0])
+        rows.append([8 * m ** 3, 6 * m ** 2, 12 * m, 1.0])
+    return np.linalg.solve(np.array(rows), np.array(y))[0]
+
+
+def _golden_tersoff():
+    vals = {}
+    with open(os.path.join(GOLDEN, "tersoff_si_c_1988.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v, _ = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+@pytest.mark.slow
+def test_tersoff_published_bulk_properties(O):
+    g = _golden_tersoff()
+    a0 = g["lattice_constant"]
+    p = _tersoff_params(O)
+    e0 = _bulk_energy_per_atom(O, p, a0)
+    assert abs(e0 + g["cohesive_energy"]) < 0.005, e0
+    # equilibrium lattice constant and bulk modulus from E(a)
+    h = 0.01
+    em = _bulk_energy_per_atom(O, p, a0 - h)
+    ep = _bulk_energy_per_atom(O, p, a0 + h)
+    dE = (ep - em) / (2 * h)
+    d2E = (ep - 2 * e0 + em) / h ** 2
+    a_eq = a0 - dE / d2E
+    assert abs(a_eq - a0) < 0.003, a_eq
+    # B = V d2E/dV2 with V = a^3/8 per atom at dE/da = 0: B = 8 E''(a) / (9 a)
+    B = 8.0 / (9.0 * a0) * d2E * 1.602176634  # eV/A^3 -> Mbar
+    assert abs(B / g["bulk_modulus"] - 1) < 0.03, B
+
+
+def test_tersoff_dimer_limit(O):
+    """For an isolated pair ζ = 0, so b = 1 and E = f_R + f_A inside R - D:
+    a minimum at r_e = ln(lam1 A / (lam2 B)) / (lam1 - lam2)."""
+    p = _tersoff_params(O)
+    t = workload("as10kev_si_300k_tersoff")["tersoff"]
+    re = np.log(t["lam1"] * t["A"] / (t["lam2"] * t["B"])) / (t["lam1"] - t["lam2"])
+    assert 1.5 < re < t["R"] - t["D"]
+
+    def E(r):
+        return O.forces(p, [1e4, 1e4, 1e4], [[0, 0, 0], [r, 0, 0]], [0, 0], with_ion=False)[0]
+
+    h = 1e-5
+    assert abs((E(re + h) - E(re - h)) / (2 * h)) < 1e-7
+    # the blend makes the pair pure ZBL (Si-Si) below 1.0 A
+    for r in (0.3, 0.6, 0.99):
+        V, _ = O.zbl(14.0, 14.0, r)
+        assert abs(E(r) - V) < 1e-9 * V
+    # beyond the cutoff the pair does not interact
+    assert E(t["R"] + t["D"] + 1e-6) == 0.0
+
+
+def test_tersoff_zero_force_on_perfect_lattice(O):
+    p = _tersoff_params(O, a=5.431)
+    X = _diamond_block(5.431, 3)
+    _, _, F, _ = O.forces(p, [1e4, 1e4, 1e4], X, np.zeros(len(X), dtype=np.int32), with_ion=False)
+    # atoms whose whole second-neighbour shell (Tersoff reaches 2 x 3.0 A) is
+    # inside the block
+    interior = np.all(X >= 6.0, axis=1) & np.all(X <= 3 * 5.431 - 6.0, axis=1)
+    assert interior.sum() >= 4
+    assert np.max(np.abs(F[interior])) < 1e-10
+    # the surface does feel forces
+    assert np.max(np.abs(F)) > 1e-2
+
+
+def _fd_check(O, p, ion, X, sp, with_ion=True, h=1e-6, tol=2e-6):
+    E0, fi, fa, _ = O.forces(p, ion, X, sp, with_ion=with_ion)
+    X = np.array(X, dtype=float)
+    for j in range(len(X)):
+        for d in range(3):
+            Xp = X.copy(); Xp[j, d] += h
+            Xm = X.copy(); Xm[j, d] -= h
+            fd = -(O.forces(p, ion, Xp, sp, with_ion=with_ion)[0] - O.forces(p, ion, Xm, sp, with_ion=with_ion)[0]) / (2 * h)
+            assert abs(fd - fa[j, d]) <= tol * max(1.0, abs(fa[j, d])), (j, d, fd, fa[j, d])
+    if with_ion:
+        for d in range(3):
+            ip = np.array(ion, dtype=float); ip[d] += h
+            im = np.array(ion, dtype=float); im[d] -= h
+            fd = -(O.forces(p, ip, X, sp)[0] - O.forces(p, im, X, sp)[0]) / (2 * h)
+            assert abs(fd - fi[d]) <= tol * max(1.0, abs(fi[d])), (d, fd, fi[d])
+
+
+def test_tersoff_and_ion_forces_match_finite_differences(O):
+    """Brute force on a 2x2x2-cell disordered Si cluster (64 atoms) with an As
+    ion inside, including a short Si-Si pair inside the ZBL blend region."""
+    p = O.params(workload("as10kev_si_300k_tersoff", sigma=0.0))
+    rng = np.random.default_rng(11)
+    X = _diamond_block(5.431, 2) + rng.normal(scale=0.12, size=(64, 3))
+    X[1] = X[0] + np.array([0.7, 0.6, 0.5])   # r = 1.1 A, inside the blend
+    ion = X[20] + np.array([0.9, -0.4, 0.3])
+    _fd_check(O, p, ion, X, np.zeros(64, dtype=np.int32))
+
+
+def _fluorite_block(a, m):
+    fcc = np.array([[0, 0, 0], [0, 2, 2], [2, 0, 2], [2, 2, 0]], dtype=float) / 4.0
+    an = np.array([[i, j, k] for i in (1, 3) for j in (1, 3) for k in (1, 3)], dtype=float) / 4.0
+    basis = np.vstack([fcc, an])
+    sp = np.array([0] * 4 + [1] * 8, dtype=np.int32)
+    pts = [(basis + [i, j, k]) * a for i in range(m) for j in range(m) for k in range(m)]
+    return np.vstack(pts), np.tile(sp, m ** 3)
+
+
+def _buck_params(O):
+    return O.params(workload("ar30kev_ceo2_300k_buck", sigma=0.0))
+
+
+def test_buckingham_zero_force_on_perfect_fluorite(O):
+    p = _buck_params(O)
+    X, sp = _fluorite_block(5.411, 4)
+    _, _, F, _ = O.forces(p, [1e4, 1e4, 1e4], X, sp, with_ion=False)
+    # atoms with the whole 5 A cutoff sphere inside the block
+    interior = np.all(X >= 5.0, axis=1) & np.all(X <= 4 * 5.411 - 5.0, axis=1)
+    assert interior.sum() >= 1
+    assert np.max(np.abs(F[interior])) < 1e-10
+
+
+def test_buckingham_forces_match_finite_differences(O):
+    p = _buck_params(O)
+    X, sp = _fluorite_block(5.411, 1)
+    rng = np.random.default_rng(5)
+    X = X + rng.normal(scale=0.1, size=X.shape)
+    X[5] = X[4] + np.array([0.5, 0.4, 0.3])   # O-O inside the ZBL blend
+    ion = X[2] + np.array([0.8, 0.2, -0.5])
+    _fd_check(O, p, ion, X, sp)

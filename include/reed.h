@@ -1,0 +1,251 @@
+/*
+ * reed.h -- C ABI of the GB300 REED-MD track stepper.
+ *
+ * REED-MD (Rare-Event-Enhanced Domain-following Molecular Dynamics) follows
+ * many independent ion tracks through a crystal (Jeon & Gronbech-Jensen,
+ * "Efficient Parallel Algorithm for Statistical Ion Track Simulations in
+ * Crystalline Materials", Sec. 2).  Each track is a small molecular-dynamics
+ * system: the ion plus an n^3-cell window of target atoms that moves with the
+ * ion (cells behind it are dropped, statistically realised cells are created
+ * ahead, Fig. "moving cell"); ion-target forces use the universal ZBL
+ * screening; target-target forces are Tersoff (Si) or short-range pairs; the
+ * ion feels electronic stopping; the integrator is velocity Verlet with an
+ * adaptive step (Sec. 2, Fig. "dt_E").  Tracks are split at cloning depths
+ * and carry weights 2^-k (Sec. 2, Fig. "split"); cloning depths are frozen
+ * while a track runs (Sec. 3).  The paper's MPI host-client feedback (Sec.
+ * 3) is replaced by device-resident tallies updated with atomics.
+ *
+ * Conventions (all entry points):
+ *   - return an int status: REED_OK (0) or a negative REED_E_* code; the
+ *     message of the last failure is available from reed_last_error();
+ *   - pointers marked "host" must point to host memory; "host or device"
+ *     accepts either (copies use cudaMemcpyDefault); output buffers are always
+ *     owned by the caller and are written, never retained;
+ *   - a reed_ctx owns all device memory it uses and is not thread-safe: use
+ *     one context per host thread (and per stream);
+ *   - units: Angstrom, eV, amu, femtoseconds where stated; angles in degrees.
+ *
+ * Nothing here allocates on the caller's behalf except reed_init (the
+ * context) and reed_run (grows the context's buffers on first use).
+ */
+#ifndef REED_H
+#define REED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define REED_OK 0
+#define REED_E_ARG -1        /* an argument is out of range or inconsistent */
+#define REED_E_CUDA -2       /* a CUDA runtime call failed */
+#define REED_E_TIMEOUT -3    /* a bounded device-side wait expired */
+#define REED_E_QUEUE_FULL -4 /* clone stack capacity exceeded (clones dropped) */
+#define REED_E_NONFINITE -5  /* an ion state became NaN/Inf (track abandoned) */
+#define REED_E_NOMEM -6      /* device memory allocation failed */
+#define REED_E_SMEM -7       /* the window does not fit in shared memory */
+#define REED_E_STATE -8      /* call made in the wrong state (e.g. no run yet) */
+#define REED_E_NEIGHBOR -9   /* target neighbour list overflowed (forces truncated) */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define REED_LATTICE_DIAMOND 0   /* 8-atom cubic cell, one species (Si) */
+#define REED_LATTICE_FLUORITE 1  /* 12-atom cubic cell: cation fcc + 8 anions (Sec. 2: UO2) */
+
+#define REED_TT_NONE 0        /* target atoms feel only the ion */
+#define REED_TT_TERSOFF 1     /* Tersoff bond order + ZBL blend (species 0) */
+#define REED_TT_BUCKINGHAM 2  /* Buckingham pairs splined to ZBL */
+
+#define REED_PREC_MIXED 0  /* FP32 forces/atoms, FP64 ion position, time, tallies */
+#define REED_PREC_FP64 1   /* everything FP64 (plain path) */
+
+#define REED_BEAM_FIXED 0  /* fixed tilt, rotation uniform in [rot_lo, rot_hi) */
+#define REED_BEAM_CONE 1   /* direction uniform in solid angle within tilt of [001] */
+
+#define REED_TRACK_STOPPED 1        /* E < e_stop: tallied at its depth */
+#define REED_TRACK_BACKSCATTERED 2  /* left through the surface (z < -rc, vz < 0) */
+#define REED_TRACK_TRUNCATED 3      /* hit step_cap */
+#define REED_TRACK_FAILED 4         /* non-finite state */
+
+/* ---- configuration structs (plain data, copied by the library) -------- */
+
+/* Target lattice and window (Sec. 2 "Second"; Fig. "moving cell").  The
+ * target occupies z >= 0 with a (001) surface.  The window holds window_n^3
+ * cells around the ion's cell (odd n) or its nearest cell corner (even n).
+ * With target-target forces, frozen_margin outer cell layers are kept fixed
+ * (they provide the environment of the integrated inner cells). */
+typedef struct {
+    int32_t kind;          /* REED_LATTICE_* */
+    int32_t window_n;      /* cells per window edge, 2..6 */
+    int32_t frozen_margin; /* 0 or 1 */
+    int32_t reserved;
+    double a;              /* lattice constant, A (> 2 rc / (window_n - 1) advised) */
+    double sigma;          /* thermal displacement RMS per Cartesian coordinate, A (Sec. 4.1) */
+} reed_lattice;
+
+/* A target species: diamond uses species 0; fluorite 0 = cation, 1 = anion. */
+typedef struct {
+    double Z;  /* atomic number */
+    double M;  /* mass, amu */
+} reed_species;
+
+/* Interaction parameters.  Ion-target: ZBL universal potential (Sec. 2
+ * "First") times exp(sum_i spline_c[i] B_i(ln r)) (cubic B-splines centred on
+ * ln r = ln{0.2,0.35,0.6,1.0,1.7,3.0} A; all zero = pure ZBL), tapered to
+ * zero between r_taper and rc with a C2 quintic.  Electronic stopping (Sec. 2
+ * "Third"): drag F = -gamma (1 + s_loc (rho/rho0 - 1)) v inside z >= 0,
+ * gamma = s_e * Lindhard-Scharff, rho = sum over atoms of S(r) exp(-r/lam_loc). */
+typedef struct {
+    double rc, r_taper;          /* A */
+    double spline_c[6];
+    int32_t target_model;        /* REED_TT_* */
+    int32_t reserved;
+    double tersoff[11];          /* A B lam1 lam2 beta n c d h R D (PRB 38, 9902) */
+    double tersoff_blend[2];     /* ZBL below [0], Tersoff above [1], A */
+    double buck_A[3], buck_rho[3], buck_C[3];  /* pairs (0,0), (0,1), (1,1) */
+    double buck_cut[2];          /* taper start, cutoff, A */
+    double buck_blend[2];        /* ZBL below [0], Buckingham above [1], A */
+    double s_e, s_loc, lam_loc;  /* stopping scale, local-density weight, density length (A) */
+} reed_potentials;
+
+/* Options of one reed_run call. */
+typedef struct {
+    double dt_max_fs;        /* upper bound of the step, fs (0.1) */
+    double dx_max;           /* max step length of the fastest particle, A (0.05) */
+    double e_stop;           /* a track stops when the ion's energy drops below, eV (5) */
+    int64_t step_cap;        /* steps per track before truncation (2e6) */
+    int32_t beam_mode;       /* REED_BEAM_* */
+    int32_t precision;       /* REED_PREC_* */
+    int32_t n_thresholds;    /* cloning depths in use, 0..16 (0 = no rare-event enhancement) */
+    int32_t n_bins;          /* range histogram bins (fixed by the first run after init/reset) */
+    double thresholds[16];   /* ascending cloning depths d_1..d_k, A */
+    double bin_width;        /* A (fixed by the first run after init/reset) */
+    int64_t first_id;        /* id of the first primary of this run (ids are the RNG streams) */
+    int32_t threads_per_track; /* 0 = autotune, else 32/64/128/256 */
+    int32_t ctas_per_sm;       /* 0 = autotune / maximum occupancy */
+    int32_t record_tracks;     /* 1: keep one reed_track_record per finished track */
+    int32_t trace_tracks;      /* record the first trace_steps steps of primaries */
+    int32_t trace_steps;       /*   first_id .. first_id + trace_tracks - 1 */
+    int32_t reserved;
+    int64_t record_capacity;   /* records kept (further tracks are counted only) */
+    void* stream;              /* cudaStream_t to run on; NULL = default stream */
+} reed_run_opts;
+
+/* Per-track result (Sec. 3: "ion ranges and their statistical clone weights"). */
+typedef struct {
+    uint64_t id;        /* track id (primaries: first_id + i; clones: hashed) */
+    uint64_t primary;   /* id of the primary whose lineage it belongs to */
+    double z;           /* depth at the end of the track, A */
+    double t;           /* simulated time, tau (1 tau = 10.1805 fs) */
+    int64_t steps;      /* integration steps of this track (clones: since the split) */
+    int32_t level;      /* cloning levels passed: weight = 2^-level */
+    int32_t status;     /* REED_TRACK_* */
+} reed_track_record;
+
+typedef struct {
+    int64_t primaries, clones, tracks, steps;  /* tracks = finished tracks (primaries + clones) */
+    int64_t pair_evals;      /* ion-target pairs inside rc */
+    int64_t bond_evals;      /* target-target pair or bond terms evaluated */
+    int64_t shifts;          /* window moves */
+    int64_t rebuilds;        /* neighbour-list builds */
+    int64_t stopped, backscattered, truncated, failed;
+    int64_t dropped_clones;  /* clones lost to a full stack */
+    int64_t nb_overflow;     /* neighbour-list overflows */
+    double w_stopped, w_back, w_trunc;   /* weights */
+    double kernel_ms;        /* device time of the last reed_run */
+    int32_t threads_per_track, ctas_per_sm, grid, smem_bytes;  /* last launch */
+} reed_stats_t;
+
+typedef struct reed_ctx reed_ctx;
+
+/* Create a context for one target (lattice, species, potentials).  *out
+ * receives the context; free it with reed_destroy.  n_species must be 1 for
+ * DIAMOND and 2 for FLUORITE.  Selects the current CUDA device.  Errors:
+ * REED_E_ARG (invalid parameters), REED_E_CUDA, REED_E_NOMEM. */
+int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, int n_species,
+              const reed_potentials* pot);
+
+/* Run n_ions primary tracks (ids opt->first_id ...) of an ion (Z, M amu) at
+ * energy_eV launched at z = -rc with lateral position uniform in the (0,0)
+ * surface cell and direction from tilt_deg and rotation U[rot_deg_lo,
+ * rot_deg_hi) (or a cone of half-angle tilt_deg), Sec. 2.  Every primary is
+ * followed, with all its clones, until it stops, leaves through the surface
+ * or reaches step_cap; results accumulate into the context's tallies until
+ * reed_reset.  seed selects the random streams (Philox4x32-10 keyed by seed
+ * and track id).  Blocks until the run is finished.  opt may be NULL (all
+ * defaults: 0.1 fs, 0.05 A, 5 eV, 2e6 steps, mixed precision, no cloning,
+ * 100 bins of 10 A).  Errors: REED_E_ARG, REED_E_SMEM, REED_E_CUDA,
+ * REED_E_NOMEM; REED_E_QUEUE_FULL / REED_E_NONFINITE / REED_E_NEIGHBOR report
+ * anomalies counted in reed_stats (the run still completes). */
+int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double tilt_deg,
+             double rot_deg_lo, double rot_deg_hi, int64_t n_ions, uint64_t seed,
+             const reed_run_opts* opt);
+
+/* Weighted range profile (Sec. 2): bins_out[n_bins] (host or device, FP64)
+ * receives sum of weights 2^-level of stopped tracks per depth bin
+ * [b*w, (b+1)*w); extra3 (host or device, may be NULL) receives
+ * {stopped above the surface, stopped beyond the last bin, backscattered}.
+ * n_bins must equal the tally's bin count.  Errors: REED_E_STATE (no run),
+ * REED_E_ARG. */
+int reed_range_profile(reed_ctx* ctx, double* bins_out, int n_bins, double* extra3);
+
+/* Counters of all runs since init/reset (host pointer). */
+int reed_stats(reed_ctx* ctx, reed_stats_t* out);
+
+/* Copy up to cap per-track records (host or device) of all runs since
+ * init/reset; *n_out (host) receives the number of records kept. */
+int reed_track_records(reed_ctx* ctx, reed_track_record* out, int64_t cap, int64_t* n_out);
+
+/* Copy the trajectory trace of the last run (opt->trace_tracks x
+ * opt->trace_steps): traj (host or device) gets 8 doubles per step
+ * (x y z t vx vy vz dt; steps after a track ended are zero), anchors (host or
+ * device, may be NULL) 3 int32 window anchor indices per step. */
+int reed_trace(reed_ctx* ctx, double* traj, int32_t* anchors, int n_tracks, int n_steps);
+
+/* Zero all tallies, records and counters. */
+int reed_reset(reed_ctx* ctx);
+
+/* Message of the last failure of this context (ctx == NULL: of the last
+ * failed reed_init on this thread).  Never NULL. */
+const char* reed_last_error(reed_ctx* ctx);
+
+void reed_destroy(reed_ctx* ctx);
+
+/* ---- diagnostics: the stepper's own device functions on given inputs --- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device: n blocks; ctr 4n,
+ * key 2n, out 4n uint32 (host pointers). */
+int reed_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
+
+/* Atoms of absolute cell (ix,iy,iz) as the stepper creates them for a track
+ * with Philox key `key` (Sec. 2, Sec. 4.1): xyz_out (host, 3*12 doubles,
+ * absolute coordinates), species_out (host, 12 int32).  Returns the atom count
+ * (0 above the surface) or a negative status. */
+int reed_cell_atoms(reed_ctx* ctx, uint64_t key, int32_t ix, int32_t iy, int32_t iz,
+                    double* xyz_out, int32_t* species_out);
+
+/* Conservative forces of one configuration computed by the stepper's force
+ * pass in `precision` (REED_PREC_*): ion at ion_x (host, 3 doubles, ion
+ * (Z, M) as given), n atoms at xyz (host, 3n, absolute) with species sp
+ * (host, n).  Outputs (host): f_ion[3], f_atoms[3n], energy[1] (potential
+ * energy; may be NULL), rho[1] (local density at the ion; may be NULL).
+ * n <= the window size of the context's lattice. */
+int reed_forces(reed_ctx* ctx, int precision, double ion_Z, double ion_M, const double* ion_x, int n,
+                const double* xyz, const int32_t* sp, double* f_ion, double* f_atoms, double* energy,
+                double* rho);
+
+/* Drive the window logic along a prescribed ion path (host, 3*npts doubles):
+ * anchors_out (host, 3*npts int32) gets the window anchor after each point;
+ * at the end the window's atoms are written (host; cells_out 3*cap int32
+ * absolute home cells, basis_out cap int32, xyz_out 3*cap doubles absolute).
+ * Returns the number of atoms in the final window or a negative status. */
+int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double* path, int npts,
+                       int32_t* anchors_out, int cap, int32_t* cells_out, int32_t* basis_out,
+                       double* xyz_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REED_H */

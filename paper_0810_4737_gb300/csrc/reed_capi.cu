@@ -1,0 +1,746 @@
+// reed_capi.cu -- host implementation of the C ABI declared in include/reed.h.
+//
+// A context holds the target description and all device buffers (tallies,
+// records, clone stacks).  reed_run turns the user's description into the
+// device parameter block (every derived constant is computed here in FP64),
+// sizes the persistent launch to the GPU (CTAs per SM from the occupancy of
+// the window in shared memory, grid = SMs x CTAs/SM) and runs it on the
+// caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "reed.h"
+#include "reed_internal.h"
+
+namespace {
+
+thread_local std::string g_init_error = "no error";
+
+// Lattice bases in units of a (diamond cubic; fluorite = cation fcc + the 8
+// tetrahedral anion sites).
+const double kDiamond[8][3] = {{0, 0, 0}, {0, .5, .5}, {.5, 0, .5}, {.5, .5, 0},
+                               {.25, .25, .25}, {.25, .75, .75}, {.75, .25, .75}, {.75, .75, .25}};
+// Fluorite: cations on the fcc sites, anions on the eight (1/4,1/4,1/4)-type
+// sites.  The basis index keys the thermal-displacement stream, so this
+// order is part of the stream definition.
+const double kFluorite[12][3] = {{0, 0, 0},       {0, .5, .5},     {.5, 0, .5},     {.5, .5, 0},
+                                 {.25, .25, .25}, {.75, .25, .25}, {.25, .75, .25}, {.25, .25, .75},
+                                 {.75, .75, .25}, {.75, .25, .75}, {.25, .75, .75}, {.75, .75, .75}};
+
+// ZBL-correction knot radii (A); B-splines are centred on ln r of each.
+const double kKnots[6] = {0.2, 0.35, 0.6, 1.0, 1.7, 3.0};
+
+const double kSkin = 0.3;   // neighbour-list skin, A
+
+double screen_inv(double Z1, double Z2) { return (std::pow(Z1, 0.23) + std::pow(Z2, 0.23)) / (0.8854 * REED_BOHR); }
+
+}  // namespace
+
+struct reed_ctx {
+    int device = 0, sms = 0;
+    size_t smem_optin = 0;
+    reed_lattice lat{};
+    reed_species sp[2]{};
+    int nspec = 0;
+    reed_potentials pot{};
+    // tallies
+    int nbins = 0;
+    double bin_w = 0.0;
+    double* d_hist = nullptr;
+    unsigned long long* d_counters = nullptr;
+    double* d_wsum = nullptr;
+    unsigned long long* d_next = nullptr;
+    int* d_status = nullptr;
+    // records
+    reed_track_record* d_records = nullptr;
+    unsigned long long* d_rec_count = nullptr;
+    long long rec_cap = 0;
+    // trace
+    double* d_trace = nullptr;
+    int* d_trace_anchor = nullptr;
+    int trace_tracks = 0, trace_steps = 0;
+    // clone stacks
+    unsigned char* d_stacks = nullptr;
+    size_t stacks_bytes = 0;
+    // scratch for diagnostics
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double last_ms = 0.0;
+    LaunchCfg last_cfg{};
+    std::string err = "no error";
+};
+
+namespace {
+
+int fail(reed_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_init_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? REED_E_NOMEM : REED_E_CUDA,         \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);      \
+    } while (0)
+
+template <typename T> void fill_hot(HotParams<T>& h, const DevParams& P, const reed_ctx* ctx, double skin)
+{
+    const reed_potentials& q = ctx->pot;
+    h.a = (T)P.a;
+    for (int s = 0; s < 2; ++s) {
+        h.invM2[s] = (T)P.invM2[s];
+        h.zk[s] = (T)P.zk[s];
+        h.zia[s] = (T)P.zia[s];
+    }
+    h.rc2 = (T)(P.rc * P.rc);
+    h.rt = (T)P.rt;
+    h.inv_tw = (T)P.inv_tw;
+    h.lam_inv = (T)P.lam_inv;
+    for (int i = 0; i < 6; ++i) {
+        h.spline_c[i] = (T)P.spline_c[i];
+        h.spline_ctr[i] = (T)P.spline_ctr[i];
+    }
+    h.spline_invh = (T)P.spline_invh;
+    // Tersoff
+    const double* t = q.tersoff;
+    const double A = t[0], B = t[1], l1 = t[2], l2 = t[3], beta = t[4], n = t[5], c = t[6], d = t[7], hh = t[8],
+                 R = t[9], D = t[10];
+    h.tA = (T)A;
+    h.tB = (T)B;
+    h.tl1 = (T)l1;
+    h.tl2 = (T)l2;
+    h.tbn = (T)(n > 0 ? std::pow(beta, n) : 0.0);
+    h.tn = (T)n;
+    h.tmhn = (T)(n > 0 ? -0.5 / n : 0.0);
+    h.tc2 = (T)(c * c);
+    h.td2 = (T)(d * d);
+    h.th = (T)hh;
+    h.tR = (T)R;
+    h.tRmD = (T)(R - D);
+    h.tcut = (T)(R + D);
+    h.tq = (T)(D > 0 ? 0.5 * REED_PI / D : 0.0);
+    h.tdq = (T)(D > 0 ? -0.25 * REED_PI / D : 0.0);
+    h.tc2d2 = (T)(d != 0 ? c * c / (d * d) : 0.0);
+    h.t_blo = (T)q.tersoff_blend[0];
+    h.t_binvw = (T)(1.0 / std::max(1e-12, q.tersoff_blend[1] - q.tersoff_blend[0]));
+    h.t_zk = (T)(P.Z2[0] * P.Z2[0] * REED_E2);
+    h.t_zia = (T)screen_inv(P.Z2[0], P.Z2[0]);
+    double cut = P.tt == REED_TT_BUCKINGHAM ? q.buck_cut[1] : R + D;
+    h.rlist2 = (T)((cut + skin) * (cut + skin));
+    h.skin_half = (T)(0.5 * skin);
+    // Buckingham
+    for (int p = 0; p < 3; ++p) {
+        h.bA[p] = (T)q.buck_A[p];
+        h.brho_inv[p] = (T)(q.buck_rho[p] > 0 ? 1.0 / q.buck_rho[p] : 0.0);
+        h.bC[p] = (T)q.buck_C[p];
+        int si = p == 2 ? 1 : 0, sj = p == 0 ? 0 : 1;
+        if (ctx->nspec < 2) si = sj = 0;
+        h.b_zk[p] = (T)(ctx->sp[si].Z * ctx->sp[sj].Z * REED_E2);
+        h.b_zia[p] = (T)screen_inv(ctx->sp[si].Z, ctx->sp[sj].Z);
+    }
+    h.b_lo = (T)q.buck_blend[0];
+    h.b_binvw = (T)(1.0 / std::max(1e-12, q.buck_blend[1] - q.buck_blend[0]));
+    h.b_rt = (T)q.buck_cut[0];
+    h.b_rinvw = (T)(1.0 / std::max(1e-12, q.buck_cut[1] - q.buck_cut[0]));
+    h.b_rc2 = (T)(q.buck_cut[1] * q.buck_cut[1]);
+}
+
+int basis_count(int kind) { return kind == REED_LATTICE_FLUORITE ? 12 : 8; }
+
+// Lindhard-Scharff electronic stopping: S = k sqrt(E), k = 1.212 Z1^(7/6) Z2 /
+// ((Z1^(2/3) + Z2^(2/3))^(3/2) sqrt(M1)) eV^(1/2) A^2; as a drag on the
+// velocity, gamma = N k sqrt(M1/2) summed over target species.
+double lindhard_gamma(const reed_ctx* ctx, double Z1, double M1)
+{
+    const double vol = ctx->lat.a * ctx->lat.a * ctx->lat.a;
+    double g = 0.0;
+    for (int s = 0; s < ctx->nspec; ++s) {
+        int count = ctx->lat.kind == REED_LATTICE_FLUORITE ? (s == 0 ? 4 : 8) : 8;
+        double Z2 = ctx->sp[s].Z;
+        double den = std::pow(std::pow(Z1, 2.0 / 3.0) + std::pow(Z2, 2.0 / 3.0), 1.5);
+        double k = 1.212 * std::pow(Z1, 7.0 / 6.0) * Z2 / (den * std::sqrt(M1));
+        g += count / vol * k;
+    }
+    return ctx->pot.s_e * g * std::sqrt(M1 / 2.0);
+}
+
+// Rows of Tersoff bond storage: atoms of a perfect bulk window that are
+// integrated or within the list radius of an integrated atom, plus 25 %
+// head-room for disorder and cascades (capped at the window size).
+int bond_capacity(const DevParams& P)
+{
+    if (P.tt != REED_TT_TERSOFF) return 0;
+    if (P.margin == 0) return P.na;
+    const double rl = P.hd.tcut + kSkin;
+    std::vector<double> x;
+    std::vector<char> act;
+    for (int i = 0; i < P.n; ++i)
+        for (int j = 0; j < P.n; ++j)
+            for (int k = 0; k < P.n; ++k) {
+                int o[3] = {i, j, k};
+                bool a = true;
+                for (int d = 0; d < 3; ++d)
+                    if (o[d] < P.margin || o[d] > P.n - 1 - P.margin) a = false;
+                for (int b = 0; b < P.nb; ++b) {
+                    for (int d = 0; d < 3; ++d) x.push_back((o[d] + P.bas[b][d]) * P.a);
+                    act.push_back(a);
+                }
+            }
+    const size_t m = act.size();
+    int count = 0;
+    for (size_t i = 0; i < m; ++i) {
+        bool need = act[i];
+        for (size_t j = 0; j < m && !need; ++j) {
+            if (!act[j]) continue;
+            double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1], dz = x[3 * i + 2] - x[3 * j + 2];
+            if (dx * dx + dy * dy + dz * dz < rl * rl) need = true;
+        }
+        count += need;
+    }
+    return std::min(P.na, (int)std::ceil(1.25 * count) + 32);
+}
+
+int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, double tilt, double rlo, double rhi,
+                const reed_run_opts& o)
+{
+    std::memset(&P, 0, sizeof(P));
+    const reed_lattice& L = ctx->lat;
+    P.kind = L.kind;
+    P.n = L.window_n;
+    P.margin = L.frozen_margin;
+    P.nb = basis_count(L.kind);
+    P.na = P.n * P.n * P.n * P.nb;
+    P.nspec = ctx->nspec;
+    P.half_n = P.n / 2;
+    P.a = L.a;
+    P.inv_a = 1.0 / L.a;
+    P.sigma = L.sigma;
+    P.anchor_shift = (P.n % 2 == 0) ? 0.5 : 0.0;
+    for (int b = 0; b < P.nb; ++b) {
+        for (int d = 0; d < 3; ++d)
+            P.bas[b][d] = L.kind == REED_LATTICE_FLUORITE ? kFluorite[b][d] : kDiamond[b][d];
+        P.bspec[b] = (L.kind == REED_LATTICE_FLUORITE && b >= 4) ? 1 : 0;
+    }
+    for (int s = 0; s < 2; ++s) {
+        const reed_species& q = ctx->sp[s < ctx->nspec ? s : 0];
+        P.Z2[s] = q.Z;
+        P.M2[s] = q.M;
+        P.invM2[s] = 1.0 / q.M;
+        P.zk[s] = Z1 * q.Z * REED_E2;
+        P.zia[s] = screen_inv(Z1, q.Z);
+    }
+    P.Z1 = Z1;
+    P.M1 = M1;
+    P.invM1 = 1.0 / M1;
+    const reed_potentials& q = ctx->pot;
+    P.rc = q.rc;
+    P.rt = q.r_taper;
+    P.rc2 = q.rc * q.rc;
+    P.inv_tw = 1.0 / (q.rc - q.r_taper);
+    P.spline_on = 0;
+    for (int i = 0; i < 6; ++i) {
+        P.spline_c[i] = q.spline_c[i];
+        P.spline_ctr[i] = std::log(kKnots[i]);
+        if (q.spline_c[i] != 0.0) P.spline_on = 1;
+    }
+    P.spline_invh = 5.0 / (std::log(kKnots[5]) - std::log(kKnots[0]));
+    P.tt = q.target_model;
+    P.gamma = lindhard_gamma(ctx, Z1, M1);
+    P.s_loc = q.s_loc;
+    P.lam_inv = 1.0 / q.lam_loc;
+    P.rho0_inv = 1.0 / (P.nb / (L.a * L.a * L.a) * 8.0 * REED_PI * q.lam_loc * q.lam_loc * q.lam_loc);
+    P.rho_on = q.s_loc != 0.0;
+    P.dt_max = o.dt_max_fs / REED_TAU_FS;
+    P.dx_max = o.dx_max;
+    P.e_stop = o.e_stop;
+    P.step_cap = o.step_cap;
+    P.v0 = std::sqrt(2.0 * E / M1);
+    P.tilt = tilt * REED_PI / 180.0;
+    P.rot_lo = rlo * REED_PI / 180.0;
+    P.rot_span = (rhi - rlo) * REED_PI / 180.0;
+    P.cos_tmax = std::cos(P.tilt);
+    P.beam_mode = o.beam_mode;
+    P.nthr = o.n_thresholds;
+    for (int i = 0; i < o.n_thresholds; ++i) P.thr[i] = o.thresholds[i];
+    P.nbins = ctx->nbins;
+    P.bin_w = ctx->bin_w;
+    P.first_id = o.first_id;
+    fill_hot<float>(P.hf, P, ctx, kSkin);
+    fill_hot<double>(P.hd, P, ctx, kSkin);
+    P.bond_cap = bond_capacity(P);
+    return REED_OK;
+}
+
+reed_run_opts default_opts()
+{
+    reed_run_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.dt_max_fs = 0.1;
+    o.dx_max = 0.05;
+    o.e_stop = 5.0;
+    o.step_cap = 2000000;
+    o.n_bins = 100;
+    o.bin_width = 10.0;
+    return o;
+}
+
+template <typename T> int dev_alloc(reed_ctx* ctx, T** p, size_t bytes)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    CK(cudaMalloc((void**)p, bytes));
+    return REED_OK;
+}
+
+int ensure_tallies(reed_ctx* ctx, int nbins, double bin_w)
+{
+    if (ctx->d_hist) {
+        if (nbins != ctx->nbins || bin_w != ctx->bin_w)
+            return fail(ctx, REED_E_ARG, "histogram is %d x %g A since the last reset; got %d x %g", ctx->nbins,
+                        ctx->bin_w, nbins, bin_w);
+        return REED_OK;
+    }
+    ctx->nbins = nbins;
+    ctx->bin_w = bin_w;
+    int rc;
+    if ((rc = dev_alloc(ctx, &ctx->d_hist, sizeof(double) * (nbins + 3)))) return rc;
+    CK(cudaMemset(ctx->d_hist, 0, sizeof(double) * (nbins + 3)));
+    return REED_OK;
+}
+
+bool valid_threads(int t) { return t == 32 || t == 64 || t == 128 || t == 256; }
+
+}  // namespace
+
+extern "C" {
+
+int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, int n_species,
+              const reed_potentials* pot)
+{
+    reed_ctx* ctx = nullptr;
+    if (!out || !lat || !sp || !pot) return fail(nullptr, REED_E_ARG, "reed_init: null argument");
+    *out = nullptr;
+    if (lat->kind != REED_LATTICE_DIAMOND && lat->kind != REED_LATTICE_FLUORITE)
+        return fail(nullptr, REED_E_ARG, "unknown lattice kind %d", lat->kind);
+    if (lat->window_n < 2 || lat->window_n > 6) return fail(nullptr, REED_E_ARG, "window_n must be 2..6");
+    if (lat->frozen_margin < 0 || 2 * lat->frozen_margin >= lat->window_n)
+        return fail(nullptr, REED_E_ARG, "frozen_margin must be 0 or 1 and leave an integrated core");
+    if (!(lat->a > 0.5) || !(lat->sigma >= 0.0)) return fail(nullptr, REED_E_ARG, "invalid lattice constant or sigma");
+    int need = lat->kind == REED_LATTICE_FLUORITE ? 2 : 1;
+    if (n_species != need) return fail(nullptr, REED_E_ARG, "lattice needs %d species, got %d", need, n_species);
+    for (int s = 0; s < n_species; ++s)
+        if (!(sp[s].Z > 0) || !(sp[s].M > 0)) return fail(nullptr, REED_E_ARG, "species %d: Z and M must be > 0", s);
+    if (!(pot->rc > 0) || !(pot->r_taper >= 0) || !(pot->r_taper < pot->rc))
+        return fail(nullptr, REED_E_ARG, "need 0 <= r_taper < rc");
+    if (pot->target_model != REED_TT_NONE && pot->target_model != REED_TT_TERSOFF)
+        return fail(nullptr, REED_E_ARG, "target model %d is not available", pot->target_model);
+    if (pot->target_model == REED_TT_TERSOFF && lat->kind != REED_LATTICE_DIAMOND)
+        return fail(nullptr, REED_E_ARG, "Tersoff needs the one-species diamond lattice");
+    if (!(pot->lam_loc > 0)) return fail(nullptr, REED_E_ARG, "lam_loc must be > 0");
+    int na = lat->window_n * lat->window_n * lat->window_n * basis_count(lat->kind);
+    if (na > 65535) return fail(nullptr, REED_E_ARG, "window too large");
+
+    ctx = new reed_ctx();
+    ctx->lat = *lat;
+    ctx->nspec = n_species;
+    for (int s = 0; s < n_species; ++s) ctx->sp[s] = sp[s];
+    ctx->pot = *pot;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&ctx->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, REED_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    ctx->smem_optin = (size_t)optin;
+    if (cudaMalloc((void**)&ctx->d_counters, sizeof(unsigned long long) * REED_NCOUNT) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_wsum, sizeof(double) * 4) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_next, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_rec_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        reed_destroy(ctx);
+        return fail(nullptr, REED_E_NOMEM, "device allocation failed");
+    }
+    cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT);
+    cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4);
+    cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long));
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        reed_destroy(ctx);
+        return fail(nullptr, REED_E_CUDA, "%s", cudaGetErrorString(e));
+    }
+    *out = ctx;
+    return REED_OK;
+}
+
+int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double tilt_deg, double rot_deg_lo,
+             double rot_deg_hi, int64_t n_ions, uint64_t seed, const reed_run_opts* opt)
+{
+    if (!ctx) return REED_E_ARG;
+    const reed_run_opts o = opt ? *opt : default_opts();
+    if (!(ion_Z > 0) || !(ion_M > 0) || !(energy_eV > 0)) return fail(ctx, REED_E_ARG, "ion Z, M, energy must be > 0");
+    if (n_ions < 0) return fail(ctx, REED_E_ARG, "n_ions < 0");
+    if (!(o.dt_max_fs > 0) || !(o.dx_max > 0) || !(o.e_stop >= 0) || o.step_cap < 1)
+        return fail(ctx, REED_E_ARG, "invalid integrator options");
+    if (o.n_thresholds < 0 || o.n_thresholds > REED_MAX_THR) return fail(ctx, REED_E_ARG, "n_thresholds must be 0..16");
+    for (int i = 1; i < o.n_thresholds; ++i)
+        if (!(o.thresholds[i] > o.thresholds[i - 1])) return fail(ctx, REED_E_ARG, "thresholds must ascend");
+    if (o.n_bins < 1 || !(o.bin_width > 0)) return fail(ctx, REED_E_ARG, "invalid histogram");
+    if (o.beam_mode != REED_BEAM_FIXED && o.beam_mode != REED_BEAM_CONE) return fail(ctx, REED_E_ARG, "beam_mode");
+    if (o.precision != REED_PREC_MIXED && o.precision != REED_PREC_FP64) return fail(ctx, REED_E_ARG, "precision");
+    if (o.threads_per_track && !valid_threads(o.threads_per_track))
+        return fail(ctx, REED_E_ARG, "threads_per_track must be 0, 32, 64, 128 or 256");
+    if (o.ctas_per_sm < 0 || o.trace_tracks < 0 || o.trace_steps < 0 || o.record_capacity < 0)
+        return fail(ctx, REED_E_ARG, "negative option");
+    int rc;
+    if ((rc = ensure_tallies(ctx, o.n_bins, o.bin_width))) return rc;
+    cudaStream_t st = (cudaStream_t)o.stream;
+
+    DevParams P;
+    make_params(ctx, P, ion_Z, ion_M, energy_eV, tilt_deg, rot_deg_lo, rot_deg_hi, o);
+    P.seed = seed;
+    P.n_primaries = n_ions;
+    P.trace_tracks = o.trace_tracks;
+    P.trace_steps = o.trace_steps;
+    P.record = o.record_tracks ? 1 : 0;
+
+    // records (kept across runs until reset; capacity fixed by the first run)
+    if (P.record) {
+        if (!ctx->d_records) {
+            ctx->rec_cap = o.record_capacity > 0 ? o.record_capacity : std::max<int64_t>(1024, 4 * n_ions);
+            if ((rc = dev_alloc(ctx, &ctx->d_records, sizeof(reed_track_record) * ctx->rec_cap))) return rc;
+        }
+        P.record_cap = ctx->rec_cap;
+    }
+    // trace buffers (per run)
+    ctx->trace_tracks = o.trace_tracks;
+    ctx->trace_steps = o.trace_steps;
+    if (o.trace_tracks > 0 && o.trace_steps > 0) {
+        size_t m = (size_t)o.trace_tracks * o.trace_steps;
+        if ((rc = dev_alloc(ctx, &ctx->d_trace, sizeof(double) * 8 * m))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->d_trace_anchor, sizeof(int) * 3 * m))) return rc;
+        CK(cudaMemsetAsync(ctx->d_trace, 0, sizeof(double) * 8 * m, st));
+        CK(cudaMemsetAsync(ctx->d_trace_anchor, 0, sizeof(int) * 3 * m, st));
+    }
+
+    // launch shape
+    const int tt = P.tt;
+    const bool f64 = o.precision == REED_PREC_FP64;
+    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap) : reed_f32::smem_bytes(tt, P.na, P.bond_cap);
+    if (smem > ctx->smem_optin)
+        return fail(ctx, REED_E_SMEM, "window of %d atoms needs %zu B of shared memory (max %zu)", P.na, smem,
+                    ctx->smem_optin);
+    LaunchCfg L;
+    L.threads = o.threads_per_track ? o.threads_per_track : (tt == REED_TT_NONE ? 64 : 256);
+    L.smem = smem;
+    int occ = 0;
+    CK(f64 ? reed_f64::occupancy(tt, L.threads, smem, &occ) : reed_f32::occupancy(tt, L.threads, smem, &occ));
+    if (occ < 1) return fail(ctx, REED_E_SMEM, "kernel does not fit on an SM (%zu B shared, %d threads)", smem, L.threads);
+    L.ctas_per_sm = o.ctas_per_sm ? std::min(o.ctas_per_sm, occ) : occ;
+    L.grid = ctx->sms * L.ctas_per_sm;
+
+    // clone stacks: one record per cloning level per CTA
+    DevBuf B;
+    std::memset(&B, 0, sizeof(B));
+    B.entry_bytes = f64 ? reed_f64::entry_bytes(tt, P.na) : reed_f32::entry_bytes(tt, P.na);
+    B.stack_depth = P.nthr;
+    B.stack_stride = B.entry_bytes * (size_t)std::max(P.nthr, 1);
+    if (P.nthr > 0) {
+        size_t need = B.stack_stride * (size_t)L.grid;
+        if (need > ctx->stacks_bytes) {
+            if ((rc = dev_alloc(ctx, &ctx->d_stacks, need))) return rc;
+            ctx->stacks_bytes = need;
+        }
+        B.stacks = ctx->d_stacks;
+    }
+    B.hist = ctx->d_hist;
+    B.counters = ctx->d_counters;
+    B.wsum = ctx->d_wsum;
+    B.next = ctx->d_next;
+    B.records = ctx->d_records;
+    B.record_count = ctx->d_rec_count;
+    B.trace = ctx->d_trace;
+    B.trace_anchor = ctx->d_trace_anchor;
+    B.status = ctx->d_status;
+
+    CK(cudaMemsetAsync(ctx->d_next, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+    CK(cudaEventRecord(ctx->ev0, st));
+    if (n_ions > 0) CK(f64 ? reed_f64::launch_track(tt, P, B, L, st) : reed_f32::launch_track(tt, P, B, L, st));
+    CK(cudaEventRecord(ctx->ev1, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    ctx->last_ms = ms;
+    ctx->last_cfg = L;
+    int status = 0;
+    CK(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status & ERR_NONFINITE) return fail(ctx, REED_E_NONFINITE, "a track became non-finite (see reed_stats)");
+    if (status & ERR_QUEUE) return fail(ctx, REED_E_QUEUE_FULL, "clone stack overflow: clones dropped");
+    if (status & ERR_NEIGHBOR) return fail(ctx, REED_E_NEIGHBOR, "neighbour list overflow (see reed_stats)");
+    return REED_OK;
+}
+
+int reed_range_profile(reed_ctx* ctx, double* bins_out, int n_bins, double* extra3)
+{
+    if (!ctx) return REED_E_ARG;
+    if (!ctx->d_hist) return fail(ctx, REED_E_STATE, "no run since init/reset");
+    if (n_bins != ctx->nbins || !bins_out) return fail(ctx, REED_E_ARG, "expected %d bins", ctx->nbins);
+    CK(cudaMemcpy(bins_out, ctx->d_hist, sizeof(double) * n_bins, cudaMemcpyDefault));
+    if (extra3) CK(cudaMemcpy(extra3, ctx->d_hist + n_bins, sizeof(double) * 3, cudaMemcpyDefault));
+    return REED_OK;
+}
+
+int reed_stats(reed_ctx* ctx, reed_stats_t* out)
+{
+    if (!ctx || !out) return REED_E_ARG;
+    unsigned long long c[REED_NCOUNT];
+    double w[4];
+    CK(cudaMemcpy(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(w, ctx->d_wsum, sizeof(w), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    out->primaries = (int64_t)c[C_PRIMARIES];
+    out->clones = (int64_t)c[C_CLONES];
+    out->tracks = (int64_t)c[C_TRACKS];
+    out->steps = (int64_t)c[C_STEPS];
+    out->pair_evals = (int64_t)c[C_PAIRS];
+    out->bond_evals = (int64_t)c[C_BONDS];
+    out->shifts = (int64_t)c[C_SHIFTS];
+    out->rebuilds = (int64_t)c[C_REBUILDS];
+    out->dropped_clones = (int64_t)c[C_DROPPED];
+    out->nb_overflow = (int64_t)c[C_NBOVF];
+    out->failed = (int64_t)c[C_FAILED];
+    out->stopped = (int64_t)c[C_STOP];
+    out->backscattered = (int64_t)c[C_BACK];
+    out->truncated = (int64_t)c[C_TRUNC];
+    out->w_stopped = w[W_STOPPED];
+    out->w_back = w[W_BACK];
+    out->w_trunc = w[W_TRUNC];
+    out->kernel_ms = ctx->last_ms;
+    out->threads_per_track = ctx->last_cfg.threads;
+    out->ctas_per_sm = ctx->last_cfg.ctas_per_sm;
+    out->grid = ctx->last_cfg.grid;
+    out->smem_bytes = (int32_t)ctx->last_cfg.smem;
+    return REED_OK;
+}
+
+int reed_track_records(reed_ctx* ctx, reed_track_record* out, int64_t cap, int64_t* n_out)
+{
+    if (!ctx || !n_out || cap < 0) return REED_E_ARG;
+    unsigned long long n = 0;
+    CK(cudaMemcpy(&n, ctx->d_rec_count, sizeof(n), cudaMemcpyDeviceToHost));
+    int64_t kept = std::min<int64_t>((int64_t)n, ctx->rec_cap);
+    int64_t m = std::min<int64_t>(kept, cap);
+    if (m > 0 && out) CK(cudaMemcpy(out, ctx->d_records, sizeof(reed_track_record) * m, cudaMemcpyDefault));
+    *n_out = kept;
+    return REED_OK;
+}
+
+int reed_trace(reed_ctx* ctx, double* traj, int32_t* anchors, int n_tracks, int n_steps)
+{
+    if (!ctx) return REED_E_ARG;
+    if (n_tracks != ctx->trace_tracks || n_steps != ctx->trace_steps || !ctx->d_trace)
+        return fail(ctx, REED_E_STATE, "last run traced %d x %d", ctx->trace_tracks, ctx->trace_steps);
+    size_t m = (size_t)n_tracks * n_steps;
+    if (traj) CK(cudaMemcpy(traj, ctx->d_trace, sizeof(double) * 8 * m, cudaMemcpyDefault));
+    if (anchors) CK(cudaMemcpy(anchors, ctx->d_trace_anchor, sizeof(int) * 3 * m, cudaMemcpyDefault));
+    return REED_OK;
+}
+
+int reed_reset(reed_ctx* ctx)
+{
+    if (!ctx) return REED_E_ARG;
+    if (ctx->d_hist) cudaFree(ctx->d_hist);
+    ctx->d_hist = nullptr;
+    if (ctx->d_records) cudaFree(ctx->d_records);
+    ctx->d_records = nullptr;
+    ctx->rec_cap = 0;
+    CK(cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT));
+    CK(cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4));
+    CK(cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long)));
+    return REED_OK;
+}
+
+const char* reed_last_error(reed_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+void reed_destroy(reed_ctx* ctx)
+{
+    if (!ctx) return;
+    void* ptrs[] = {ctx->d_hist, ctx->d_counters, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
+                    ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+// ---- diagnostics -------------------------------------------------------
+
+static __global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
+                                     uint32_t* __restrict__ out, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    philox10(c, key[2 * i], key[2 * i + 1]);
+    for (int k = 0; k < 4; ++k) out[4 * i + k] = c[k];
+}
+
+int reed_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n)
+{
+    reed_ctx* ctx = nullptr;
+    if (!ctr || !key || !out || n < 0) return fail(nullptr, REED_E_ARG, "reed_philox: bad argument");
+    if (n == 0) return REED_OK;
+    uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    CK(cudaMalloc((void**)&dc, 16 * n));
+    CK(cudaMalloc((void**)&dk, 8 * n));
+    CK(cudaMalloc((void**)&dout, 16 * n));
+    CK(cudaMemcpy(dc, ctr, 16 * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dk, key, 8 * n, cudaMemcpyHostToDevice));
+    philox_kernel<<<(unsigned)((n + 127) / 128), 128>>>(dc, dk, dout, n);
+    CK(cudaGetLastError());
+    CK(cudaMemcpy(out, dout, 16 * n, cudaMemcpyDeviceToHost));
+    cudaFree(dc);
+    cudaFree(dk);
+    cudaFree(dout);
+    return REED_OK;
+}
+
+namespace {
+size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+int scratch(reed_ctx* ctx, size_t bytes, void** p)
+{
+    if (bytes > ctx->scratch_bytes) {
+        if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+        ctx->d_scratch = nullptr;
+        ctx->scratch_bytes = 0;
+        CK(cudaMalloc(&ctx->d_scratch, bytes));
+        ctx->scratch_bytes = bytes;
+    }
+    *p = ctx->d_scratch;
+    return REED_OK;
+}
+
+reed_run_opts diag_opts()
+{
+    reed_run_opts o = default_opts();
+    return o;
+}
+}  // namespace
+
+int reed_cell_atoms(reed_ctx* ctx, uint64_t key, int32_t ix, int32_t iy, int32_t iz, double* xyz_out,
+                    int32_t* species_out)
+{
+    if (!ctx || !xyz_out || !species_out) return REED_E_ARG;
+    DevParams P;
+    reed_run_opts o = diag_opts();
+    make_params(ctx, P, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0, o);
+    void* s = nullptr;
+    int rc;
+    if ((rc = scratch(ctx, 512, &s))) return rc;
+    double* dx = (double*)s;
+    int* dsp = (int*)((char*)s + 36 * sizeof(double));
+    int* dn = dsp + 12;
+    CK(reed_f64::launch_cell_atoms(P, key, ix, iy, iz, dx, dsp, dn, 0));
+    int n = 0;
+    CK(cudaMemcpy(&n, dn, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(xyz_out, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(species_out, dsp, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    return n;
+}
+
+int reed_forces(reed_ctx* ctx, int precision, double ion_Z, double ion_M, const double* ion_x, int n,
+                const double* xyz, const int32_t* sp, double* f_ion, double* f_atoms, double* energy, double* rho)
+{
+    if (!ctx || !ion_x || (n > 0 && (!xyz || !sp || !f_atoms)) || !f_ion || n < 0) return REED_E_ARG;
+    DevParams P;
+    reed_run_opts o = diag_opts();
+    make_params(ctx, P, ion_Z, ion_M, 1.0, 0.0, 0.0, 0.0, o);
+    if (n > P.na) return fail(ctx, REED_E_ARG, "at most %d atoms", P.na);
+    for (int i = 0; i < n; ++i)
+        if (sp[i] < 0 || sp[i] >= ctx->nspec) return fail(ctx, REED_E_ARG, "species %d out of range", sp[i]);
+    const bool f64 = precision == REED_PREC_FP64;
+    if (P.tt == REED_TT_TERSOFF) P.bond_cap = std::max(n, 1);   // every given atom is integrated
+    size_t smem = f64 ? reed_f64::smem_bytes(P.tt, P.na, P.bond_cap) : reed_f32::smem_bytes(P.tt, P.na, P.bond_cap);
+    if (smem > ctx->smem_optin) return fail(ctx, REED_E_SMEM, "window needs %zu B shared memory", smem);
+    size_t bx = up16(sizeof(double) * 3 * (size_t)std::max(n, 1)), bs = up16(sizeof(int) * (size_t)std::max(n, 1));
+    size_t bi = up16(sizeof(double) * 3), bo = up16(sizeof(double) * (5 + 3 * (size_t)std::max(n, 1)));
+    void* s = nullptr;
+    int rc;
+    if ((rc = scratch(ctx, bx + bs + bi + bo, &s))) return rc;
+    double* dx = (double*)s;
+    int* dsp = (int*)((char*)s + bx);
+    double* dion = (double*)((char*)s + bx + bs);
+    double* dout = (double*)((char*)s + bx + bs + bi);
+    if (n > 0) {
+        CK(cudaMemcpy(dx, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dsp, sp, sizeof(int) * n, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(dion, ion_x, sizeof(double) * 3, cudaMemcpyHostToDevice));
+    CK(f64 ? reed_f64::launch_forces(P.tt, P, n, dx, dsp, dion, dout, smem, 0)
+           : reed_f32::launch_forces(P.tt, P, n, dx, dsp, dion, dout, smem, 0));
+    std::vector<double> h(5 + 3 * (size_t)n);
+    CK(cudaMemcpy(h.data(), dout, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    for (int d = 0; d < 3; ++d) f_ion[d] = h[d];
+    if (energy) *energy = h[3];
+    if (rho) *rho = h[4];
+    for (int i = 0; i < 3 * n; ++i) f_atoms[i] = h[5 + i];
+    return REED_OK;
+}
+
+int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double* path, int npts,
+                       int32_t* anchors_out, int cap, int32_t* cells_out, int32_t* basis_out, double* xyz_out)
+{
+    if (!ctx || !path || npts < 1 || !anchors_out || cap < 0) return REED_E_ARG;
+    DevParams P;
+    reed_run_opts o = diag_opts();
+    make_params(ctx, P, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0, o);
+    const bool f64 = precision == REED_PREC_FP64;
+    size_t smem = f64 ? reed_f64::smem_bytes(REED_TT_NONE, P.na, 0) : reed_f32::smem_bytes(REED_TT_NONE, P.na, 0);
+    size_t bp = sizeof(double) * 3 * npts, ba = sizeof(int) * 3 * npts;
+    size_t c = (size_t)std::max(cap, 1);
+    size_t bc = sizeof(int) * 3 * c, bb = sizeof(int) * c, bx = sizeof(double) * 3 * c;
+    void* s = nullptr;
+    int rc;
+    if ((rc = scratch(ctx, bp + ba + bc + bb + bx + 64, &s))) return rc;
+    char* q = (char*)s;
+    double* dpath = (double*)q;
+    double* dxyz = (double*)(q + bp);
+    int* danc = (int*)(q + bp + bx);
+    int* dcells = danc + 3 * npts;
+    int* dbas = dcells + 3 * c;
+    int* dn = dbas + c;
+    CK(cudaMemcpy(dpath, path, bp, cudaMemcpyHostToDevice));
+    CK(f64 ? reed_f64::launch_window_replay(P, key, dpath, npts, danc, cap, dcells, dbas, dxyz, dn, smem, 0)
+           : reed_f32::launch_window_replay(P, key, dpath, npts, danc, cap, dcells, dbas, dxyz, dn, smem, 0));
+    int n = 0;
+    CK(cudaMemcpy(&n, dn, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(anchors_out, danc, ba, cudaMemcpyDeviceToHost));
+    int m = std::min(n, cap);
+    if (m > 0) {
+        CK(cudaMemcpy(cells_out, dcells, sizeof(int) * 3 * m, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(basis_out, dbas, sizeof(int) * m, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(xyz_out, dxyz, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost));
+    }
+    return n;
+}
+
+}  // extern "C"

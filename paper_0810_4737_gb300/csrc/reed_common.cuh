@@ -1,0 +1,258 @@
+// reed_common.cuh -- device-side parameter block, buffers, math helpers and
+// the counter-based random streams of the REED-MD track stepper.
+//
+// Units: Angstrom, eV, amu; time unit tau = sqrt(amu A^2/eV) = 10.1805 fs
+// (the paper's Fig. "dt_E" quotes the time unit as 10.18 fs).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "reed.h"
+
+#define REED_TAU_FS 10.180505710
+#define REED_E2 14.399645       // e^2 / (4 pi eps0), eV A
+#define REED_BOHR 0.529177      // A
+#define REED_PI 3.14159265358979323846
+
+#define REED_MAX_BASIS 12
+#define REED_MAX_THR 16
+#define REED_MAX_WARPS 8
+#define REED_MAXNB 8            // target neighbours kept per atom (Tersoff)
+
+// slot flags carried in pos.w (exact small integers in either precision):
+//   w = species (0/1) for an integrated atom, species + 2 for a frozen atom,
+//   -1 for an empty slot (cell above the surface).
+#define REED_W_EMPTY (-1)
+
+enum { REED_NCOUNT = 16 };
+enum {
+    C_PRIMARIES = 0, C_CLONES, C_TRACKS, C_STEPS, C_PAIRS, C_BONDS, C_SHIFTS, C_REBUILDS,
+    C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_SPARE0, C_SPARE1
+};
+enum { W_STOPPED = 0, W_BACK, W_TRUNC, W_FAILED };
+
+// Hot-loop parameters in the arithmetic type of the force pass (float for
+// the mixed form, double for the plain FP64 path), so that no conversion is
+// executed per pair.
+template <typename R> struct HotParams {
+    R a;                          // lattice constant
+    R invM2[2];
+    // ion-target
+    R rc2, rt, inv_tw, zk[2], zia[2], lam_inv;
+    R spline_c[6], spline_ctr[6], spline_invh;
+    // Tersoff
+    R tA, tB, tl1, tl2, tbn, tn, tmhn, tc2, td2, th, tRmD, tcut, tq, tdq, tR, tc2d2;
+    R t_blo, t_binvw, t_zk, t_zia, rlist2, skin_half;
+    // Buckingham
+    R bA[3], brho_inv[3], bC[3], b_lo, b_binvw, b_rt, b_rinvw, b_rc2, b_zk[3], b_zia[3];
+};
+
+// Everything a launch needs, passed by value (__grid_constant__).
+struct DevParams {
+    HotParams<float> hf;
+    HotParams<double> hd;
+    // lattice and window (Sec. 2 "Second")
+    int kind, n, margin, nb, na, nspec, half_n;   // half_n = n / 2
+    double a, inv_a, sigma, anchor_shift;          // anchor_shift = 0.5 for even n
+    double bas[REED_MAX_BASIS][3];
+    int bspec[REED_MAX_BASIS];
+    double Z2[2], M2[2], invM2[2];
+    // ion
+    double Z1, M1, invM1;
+    // ion-target ZBL with taper (Sec. 2 "First")
+    double rc, rt, rc2, inv_tw;
+    double zk[2], zia[2];           // Z1 Z2 e^2, 1/a_U per target species
+    int spline_on;
+    double spline_c[6], spline_ctr[6], spline_invh;   // B-spline weights, centres (ln r), 1/width
+    // target-target
+    int tt;
+    double tA, tB, tl1, tl2, tbn, tn, tc2, td2, th, tR, tD, tcut, tc2d2;
+    double t_blo, t_bhi, t_zk, t_zia;  // Tersoff->ZBL blend, Si-Si ZBL
+    double bA[3], brho_inv[3], bC[3];
+    double b_rt, b_rc, b_lo, b_hi;
+    double b_zk[3], b_zia[3];
+    int bond_cap;                      // Tersoff bond-storage rows (needed atoms)
+    // electronic stopping (Sec. 2 "Third")
+    double gamma, s_loc, rho0_inv, lam_inv;
+    int rho_on;
+    // integrator (Sec. 2, Fig. "dt_E")
+    double dt_max, dx_max, e_stop;
+    long long step_cap;
+    // beam
+    double v0, tilt, rot_lo, rot_span, cos_tmax;
+    int beam_mode;
+    // rare-event enhancement (Sec. 2)
+    int nthr;
+    double thr[REED_MAX_THR];
+    // tallies
+    int nbins;
+    double bin_w;
+    // run
+    unsigned long long seed;
+    long long n_primaries, first_id;
+    int trace_tracks, trace_steps;
+    int record;
+    long long record_cap;
+};
+
+struct DevBuf {
+    double* hist;                   // nbins + 3 (under, over, back)
+    unsigned long long* counters;   // REED_NCOUNT
+    double* wsum;                   // W_*
+    unsigned long long* next;       // primary queue head
+    reed_track_record* records;
+    unsigned long long* record_count;
+    double* trace;                  // trace_tracks * trace_steps * 8
+    int* trace_anchor;              // trace_tracks * trace_steps * 3
+    unsigned char* stacks;          // per-CTA clone stacks
+    size_t stack_stride, entry_bytes;
+    int stack_depth;
+    int* status;                    // [0] OR of error bits
+};
+
+enum { ERR_QUEUE = 1, ERR_NONFINITE = 2, ERR_NEIGHBOR = 4 };
+
+// ---------------------------------------------------------------------------
+// Precision-generic vector and math helpers.  The FP32 forms use the SFU
+// (ex2/lg2/rsqrt/sin/cos approximations of the PTX ISA); the FP64 forms call
+// the CUDA double-precision functions.
+// ---------------------------------------------------------------------------
+template <typename R> struct alignas(16) V4 { R x, y, z, w; };
+
+template <typename R> __device__ __forceinline__ const HotParams<R>& hot(const DevParams& P);
+template <> __device__ __forceinline__ const HotParams<float>& hot<float>(const DevParams& P) { return P.hf; }
+template <> __device__ __forceinline__ const HotParams<double>& hot<double>(const DevParams& P) { return P.hd; }
+
+__device__ __forceinline__ float sfu_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_lg2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <typename R> struct Mth;
+template <> struct Mth<float> {
+    static constexpr float LOG2E = 1.4426950408889634f;
+    __device__ static __forceinline__ float exp(float x) { return sfu_ex2(x * LOG2E); }
+    // exp(-c x) with c already multiplied by log2(e)
+    __device__ static __forceinline__ float exp2n(float x) { return sfu_ex2(x); }
+    __device__ static __forceinline__ float rsqrt(float x) { return sfu_rsqrt(x); }
+    __device__ static __forceinline__ float log(float x) { return sfu_lg2(x) * 0.6931471805599453f; }
+    __device__ static __forceinline__ float pow(float x, float y) { return sfu_ex2(y * sfu_lg2(x)); }
+    __device__ static __forceinline__ float sin(float x) { return __sinf(x); }
+    __device__ static __forceinline__ float cos(float x) { return __cosf(x); }
+    __device__ static __forceinline__ float rcp(float x) { return sfu_rcp(x); }
+};
+template <> struct Mth<double> {
+    static constexpr double LOG2E = 1.4426950408889634;
+    __device__ static __forceinline__ double exp(double x) { return ::exp(x); }
+    __device__ static __forceinline__ double exp2n(double x) { return ::exp2(x); }
+    __device__ static __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
+    __device__ static __forceinline__ double log(double x) { return ::log(x); }
+    __device__ static __forceinline__ double pow(double x, double y) { return ::pow(x, y); }
+    __device__ static __forceinline__ double sin(double x) { return ::sin(x); }
+    __device__ static __forceinline__ double cos(double x) { return ::cos(x); }
+    __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
+};
+
+// ---------------------------------------------------------------------------
+// Counter-based random streams.
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products with multipliers 0xD2511F53 / 0xCD9E8D57, key
+// bumped by the Weyl constants 0x9E3779B9 / 0xBB67AE85 between rounds.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+#else
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        uint32_t a0 = hi1 ^ c[1] ^ k0, a2 = hi0 ^ c[3] ^ k1;
+        c[0] = a0; c[1] = lo1; c[2] = a2; c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// SplitMix64 finaliser (Steele, Lea, Flood 2014) used to derive stream keys.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// Philox key of track `id` under `seed`.
+__host__ __device__ __forceinline__ uint64_t track_key(uint64_t seed, uint64_t id)
+{
+    return mix64(seed + 0x9E3779B97F4A7C15ull * (id + 1ull));
+}
+// Id of the clone a track spawns when it passes cloning level `level`.
+__host__ __device__ __forceinline__ uint64_t clone_id(uint64_t parent, int level)
+{
+    return mix64(parent ^ (0xD1B54A32D192ED03ull * (uint64_t)(level + 1)));
+}
+
+#define REED_TAG_CELL 1u
+#define REED_TAG_LAUNCH 2u
+
+__device__ __forceinline__ void draw4(uint64_t key, int ix, int iy, int iz, uint32_t word, uint32_t out[4])
+{
+    out[0] = (uint32_t)ix; out[1] = (uint32_t)iy; out[2] = (uint32_t)iz; out[3] = word;
+    philox10(out, (uint32_t)key, (uint32_t)(key >> 32));
+}
+
+__device__ __forceinline__ double unit_open(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
+
+// Three normals from one Philox block by the Box-Muller transform.
+__device__ __forceinline__ void box_muller3(const uint32_t w[4], double g[3])
+{
+    double r1 = sqrt(-2.0 * log(unit_open(w[0])));
+    double r2 = sqrt(-2.0 * log(unit_open(w[2])));
+    double s1, c1, c2;
+    sincospi(2.0 * unit_open(w[1]), &s1, &c1);
+    c2 = cospi(2.0 * unit_open(w[3]));
+    g[0] = r1 * c1;
+    g[1] = r1 * s1;
+    g[2] = r2 * c2;
+}
+
+// ---------------------------------------------------------------------------
+// Warp reductions (fixed butterfly order: results are reproducible).
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T> __device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}

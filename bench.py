@@ -1,0 +1,307 @@
+"""Benchmark: batched ion-steps/s of the REED-MD track stepper on GB300.
+
+A "step" is one pass of the whole hot path over one batch: reed_run of the
+workload's primaries (4096 As ions at 10 keV into Si at 300 K, Tersoff
+target, 5x5x5-cell window) followed to the end of every track.  Each timed
+step runs a fresh batch (primary ids step*n ... ) in the mixed-precision form.
+
+Reported beside it: the plain FP64 GPU path on a sample of the same batch
+(the metric's comparison), the range-profile KS p-value between the two, the
+FP32-ALU roofline of the stepper kernel, the CPU oracle timed on the host
+cores, and an end-to-end figure through the public API with host buffers.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own shard of primaries (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched ion-steps/s on 1 GB300, chosen vs plain FP64 path, range-profile KS p>0.01"
+WORKLOAD = "as10kev_si_300k_tersoff"
+# Algorithmic FP32 work per unit (see the design notes): ZBL ion-target pair
+# 35 ops, integrated atom update 12 FMA = 24 ops, Tersoff bond-angle triplet 60 ops.
+OPS_PAIR, OPS_MOVE, OPS_TRIPLET = 35, 24, 60
+SMS, FP32_LANES = 152, 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _ks(a, b):
+    from scipy import stats
+    if len(a) < 2 or len(b) < 2:
+        return None
+    return float(stats.ks_2samp(a, b).pvalue)
+
+
+def cpu_baseline(w, n_ions, threads):
+    """The oracle on the host cores, bounded sample; ion-steps/s."""
+    from oracle import oracle as O
+    p = O.params(w)
+    t0 = time.perf_counter()
+    r = O.run(p, n_ions, seed=w["seed"], first_id=0, threads=threads, records=False)
+    dt = time.perf_counter() - t0
+    return r["steps"] / dt, r["steps"], dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_0810_4737_gb300.workloads import workload
+    w = workload(args.workload)
+    threads = os.cpu_count() or 1
+    n = args.ref_ions
+    for _ in range(args.warmup):
+        cpu_baseline(w, max(1, threads // 4), threads)
+    vals, steps_tot, t_tot = [], 0, 0.0
+    for _ in range(args.steps):
+        v, st, dt = cpu_baseline(w, n, threads)
+        vals.append(v)
+        steps_tot += st
+        t_tot += dt
+    value = steps_tot / t_tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ion-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "ions_per_step": n, "ion": "As-75", "energy_eV": w["energy"],
+                       "window_atoms": w["n"] ** 3 * 8, "sample": "%d primaries per step" % n},
+            "cpu_baseline": {"value": value, "unit": "ion-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d primaries of %s per step, FP64 C oracle, OpenMP" % (n, w["name"])},
+            "e2e": {"value": value, "unit": "ion-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--ions", type=int, default=0, help="primaries per step per GPU (0: the workload's)")
+    ap.add_argument("--fp64-ions", type=int, default=256, help="sample of the plain FP64 path")
+    ap.add_argument("--cpu-ions", type=int, default=0, help="oracle sample (0: auto, ~10-30 s)")
+    ap.add_argument("--ref-ions", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_0810_4737_gb300 import build, reed as R
+    from paper_0810_4737_gb300.workloads import workload
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    w = workload(args.workload)
+    n = args.ions or w["n_ions"]
+    stream = torch.cuda.current_stream()
+    sh = ctypes_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+
+    ctx = R.Reed(w)
+    first = rank * 10_000_000
+
+    def one(step_idx, record=False):
+        return ctx.run(n_ions=n, seed=w["seed"], first_id=first + step_idx * n, record=record, stream=sh,
+                       tolerate=(R.E_NEIGHBOR,))
+
+    for i in range(args.warmup):
+        one(i)
+    ctx.reset()
+    # ---- timed region: K steps, device-timed with CUDA events on the launch stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    kernel_ms = []
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        ev[i][0].record(stream)
+        one(args.warmup + i)
+        ev[i][1].record(stream)
+        kernel_ms.append(ctx.stats()["kernel_ms"])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st = ctx.stats()
+    tot_ms = sum(step_ms)
+    steps_done = st["steps"]
+    if ws > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        c = torch.tensor([steps_done], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        steps_done = int(c.item())
+    value = steps_done / (tot_ms * 1e-3)
+    pairs_per_s = (st["pair_evals"] + st["bond_evals"]) * ws / (tot_ms * 1e-3)
+    # roofline of the stepper kernel (FP32 ALU)
+    flops = OPS_PAIR * st["pair_evals"] + OPS_MOVE * st["atom_updates"] + OPS_TRIPLET * st["triplets"]
+    kern_s = sum(kernel_ms) * 1e-3
+    achieved = flops / kern_s / 1e12
+    peak = SMS * FP32_LANES * 2 * 2070e6 / 1e12
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if rank == 0:
+        ctx.reset()
+        t0 = time.perf_counter()
+        e2e_steps = 0
+        for i in range(args.steps):
+            ctx.run(n_ions=n, seed=w["seed"], first_id=first + (100 + i) * n, record=False, tolerate=(R.E_NEIGHBOR,))
+            bins, extra = ctx.profile()                 # device -> host
+            e2e_steps = ctx.stats()["steps"]            # device -> host
+        dt = time.perf_counter() - t0
+        import ctypes
+        h2d = ctypes.sizeof(R.reed_run_opts) + 8 * 8
+        d2h = 8 * (int(w["n_bins"]) + 3) + ctypes.sizeof(R.reed_stats_t)
+        e2e = {"value": e2e_steps / dt, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "reed_run + reed_range_profile + reed_stats per step, host wall clock"}
+    # ---- plain FP64 path on a sample, and the KS check of the two profiles
+    fp64 = None
+    if rank == 0 and args.fp64_ions > 0:
+        m = args.fp64_ions
+        with R.Reed(w) as c64, R.Reed(w) as c32:
+            c64.run(n_ions=m, seed=w["seed"], first_id=first, precision=R.PREC_FP64, stream=sh,
+                    tolerate=(R.E_NEIGHBOR,))
+            s64 = c64.stats()
+            r64 = c64.records()
+            c32.run(n_ions=m, seed=w["seed"], first_id=first, precision=R.PREC_MIXED, stream=sh,
+                    tolerate=(R.E_NEIGHBOR,))
+            s32 = c32.stats()
+            r32 = c32.records()
+        z64 = r64["z"][r64["status"] == R.STOPPED]
+        z32 = r32["z"][r32["status"] == R.STOPPED]
+        fp64 = {"value": s64["steps"] / (s64["kernel_ms"] * 1e-3), "unit": "ion-steps/s",
+                "mixed_same_sample": s32["steps"] / (s32["kernel_ms"] * 1e-3), "sample_ions": m,
+                "ks_p_mixed_vs_fp64": _ks(z32, z64),
+                "mean_depth_A": [float(np.mean(z32)) if len(z32) else None, float(np.mean(z64)) if len(z64) else None]}
+    # ---- CPU oracle on the host cores (bounded sample)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        ci = args.cpu_ions or max(threads, 16)
+        v, stp, dt = cpu_baseline(w, ci, threads)
+        cpu = {"value": v, "unit": "ion-steps/s", "cores": threads, "kind": "oracle",
+               "sample": "%d primaries of %s (%d ion-steps, %.1f s), FP64 C oracle with OpenMP" % (ci, w["name"], stp, dt)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "ion-steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "ions_per_step_per_gpu": n, "ion": "As-75", "energy_eV": w["energy"],
+                       "target": "Si(100) 300 K sigma 0.076 A, Tersoff+ZBL", "window_atoms": w["n"] ** 3 * 8,
+                       "parallelism": "replicas (independent primaries per GPU)",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "precision": "FP32 forces/atoms, FP64 ion position/time/energy accumulation"},
+            "pair_forces_per_s": pairs_per_s,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                         "kernel": "reed_track_kernel<float, TERSOFF>",
+                         "kernel_ms_per_launch": sum(kernel_ms) / len(kernel_ms)},
+            "fp64_path": fp64,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "stats": {k: st[k] for k in ("primaries", "tracks", "steps", "pair_evals", "bond_evals", "triplets",
+                                         "atom_updates", "shifts", "rebuilds", "nb_overflow", "bond_cap_overflow",
+                                         "threads_per_track", "ctas_per_sm", "grid", "smem_bytes")},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def ctypes_stream(stream):
+    """cudaStream_t handle of a torch stream, for the C ABI."""
+    return int(stream.cuda_stream) or None
+
+
+if __name__ == "__main__":
+    sys.exit(main())

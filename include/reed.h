@@ -132,13 +132,14 @@ typedef struct {
     void* stream;              /* cudaStream_t to run on; NULL = default stream */
 } reed_run_opts;
 
-/* Per-track result (Sec. 3: "ion ranges and their statistical clone weights"). */
+/* Per-track result: the depth and weight of one finished track (Sec. 3, result messages). */
 typedef struct {
     uint64_t id;        /* track id (primaries: first_id + i; clones: hashed) */
     uint64_t primary;   /* id of the primary whose lineage it belongs to */
     double z;           /* depth at the end of the track, A */
     double t;           /* simulated time, tau (1 tau = 10.1805 fs) */
-    int64_t steps;      /* integration steps of this track (clones: since the split) */
+    int64_t steps;      /* integration steps of the track's history (a clone counts its
+                           parent's steps before the split; step_cap applies to this) */
     int32_t level;      /* cloning levels passed: weight = 2^-level */
     int32_t status;     /* REED_TRACK_* */
 } reed_track_record;
@@ -151,7 +152,10 @@ typedef struct {
     int64_t rebuilds;        /* neighbour-list builds */
     int64_t stopped, backscattered, truncated, failed;
     int64_t dropped_clones;  /* clones lost to a full stack */
-    int64_t nb_overflow;     /* neighbour-list overflows */
+    int64_t nb_overflow;     /* neighbour-list overflows (bonds beyond the per-atom capacity) */
+    int64_t bond_cap_overflow; /* atoms left without Tersoff bond storage */
+    int64_t triplets;        /* Tersoff bond-angle (zeta) terms evaluated */
+    int64_t atom_updates;    /* integrated target-atom updates (atoms x steps) */
     double w_stopped, w_back, w_trunc;   /* weights */
     double kernel_ms;        /* device time of the last reed_run */
     int32_t threads_per_track, ctas_per_sm, grid, smem_bytes;  /* last launch */
@@ -175,7 +179,8 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
  * reed_reset.  seed selects the random streams (Philox4x32-10 keyed by seed
  * and track id).  Blocks until the run is finished.  opt may be NULL (all
  * defaults: 0.1 fs, 0.05 A, 5 eV, 2e6 steps, mixed precision, no cloning,
- * 100 bins of 10 A).  Errors: REED_E_ARG, REED_E_SMEM, REED_E_CUDA,
+ * 100 bins of 10 A).  With record_tracks and record_capacity 0 the record
+ * buffer holds n_ions * (1 + 4 n_thresholds) + 1024 records.  Errors: REED_E_ARG, REED_E_SMEM, REED_E_CUDA,
  * REED_E_NOMEM; REED_E_QUEUE_FULL / REED_E_NONFINITE / REED_E_NEIGHBOR report
  * anomalies counted in reed_stats (the run still completes). */
 int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double tilt_deg,

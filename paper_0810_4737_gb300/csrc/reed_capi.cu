@@ -158,6 +158,16 @@ template <typename T> void fill_hot(HotParams<T>& h, const DevParams& P, const r
     h.b_rt = (T)q.buck_cut[0];
     h.b_rinvw = (T)(1.0 / std::max(1e-12, q.buck_cut[1] - q.buck_cut[0]));
     h.b_rc2 = (T)(q.buck_cut[1] * q.buck_cut[1]);
+    h.dt_max = (T)P.dt_max;
+    h.dx_max = (T)P.dx_max;
+    h.e_stop = (T)P.e_stop;
+    h.M1 = (T)P.M1;
+    h.invM1 = (T)P.invM1;
+    h.gamma = (T)P.gamma;
+    h.s_loc = (T)P.s_loc;
+    h.rho0_inv = (T)P.rho0_inv;
+    h.anchor_lo = (T)(-P.anchor_shift * P.a);
+    h.anchor_hi = (T)((1.0 - P.anchor_shift) * P.a);
 }
 
 int basis_count(int kind) { return kind == REED_LATTICE_FLUORITE ? 12 : 8; }
@@ -423,7 +433,8 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     // records (kept across runs until reset; capacity fixed by the first run)
     if (P.record) {
         if (!ctx->d_records) {
-            ctx->rec_cap = o.record_capacity > 0 ? o.record_capacity : std::max<int64_t>(1024, 4 * n_ions);
+            ctx->rec_cap = o.record_capacity > 0 ? o.record_capacity
+                                                 : n_ions * (1 + 4 * (int64_t)o.n_thresholds) + 1024;
             if ((rc = dev_alloc(ctx, &ctx->d_records, sizeof(reed_track_record) * ctx->rec_cap))) return rc;
         }
         P.record_cap = ctx->rec_cap;
@@ -525,6 +536,9 @@ int reed_stats(reed_ctx* ctx, reed_stats_t* out)
     out->rebuilds = (int64_t)c[C_REBUILDS];
     out->dropped_clones = (int64_t)c[C_DROPPED];
     out->nb_overflow = (int64_t)c[C_NBOVF];
+    out->bond_cap_overflow = (int64_t)c[C_CAPOVF];
+    out->triplets = (int64_t)c[C_TRIPLETS];
+    out->atom_updates = (int64_t)c[C_MOVED];
     out->failed = (int64_t)c[C_FAILED];
     out->stopped = (int64_t)c[C_STOP];
     out->backscattered = (int64_t)c[C_BACK];

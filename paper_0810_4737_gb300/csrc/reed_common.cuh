@@ -18,17 +18,17 @@
 #define REED_MAX_BASIS 12
 #define REED_MAX_THR 16
 #define REED_MAX_WARPS 8
-#define REED_MAXNB 8            // target neighbours kept per atom (Tersoff)
+#define REED_MAXNB 12           // target neighbours kept per atom
 
 // slot flags carried in pos.w (exact small integers in either precision):
 //   w = species (0/1) for an integrated atom, species + 2 for a frozen atom,
 //   -1 for an empty slot (cell above the surface).
 #define REED_W_EMPTY (-1)
 
-enum { REED_NCOUNT = 16 };
+enum { REED_NCOUNT = 18 };
 enum {
     C_PRIMARIES = 0, C_CLONES, C_TRACKS, C_STEPS, C_PAIRS, C_BONDS, C_SHIFTS, C_REBUILDS,
-    C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_SPARE0, C_SPARE1
+    C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_CAPOVF, C_TRIPLETS, C_MOVED, C_SPARE
 };
 enum { W_STOPPED = 0, W_BACK, W_TRUNC, W_FAILED };
 
@@ -46,6 +46,8 @@ template <typename R> struct HotParams {
     R t_blo, t_binvw, t_zk, t_zia, rlist2, skin_half;
     // Buckingham
     R bA[3], brho_inv[3], bC[3], b_lo, b_binvw, b_rt, b_rinvw, b_rc2, b_zk[3], b_zia[3];
+    // ion step
+    R dt_max, dx_max, e_stop, M1, invM1, gamma, s_loc, rho0_inv, anchor_lo, anchor_hi;
 };
 
 // Everything a launch needs, passed by value (__grid_constant__).

@@ -103,12 +103,14 @@ template <typename R> __device__ __forceinline__ R ters_fc(const HotParams<R>& H
     return R(0.5) - R(0.5) * Mth<R>::sin(q);
 }
 
+// g is evaluated as 1 + (C^2/d^2) q^2 / (d^2 + q^2), q = h - cos theta, which
+// equals the textbook form without its cancellation (C^2/d^2 ~ 4e7 for Si).
 template <typename R> __device__ __forceinline__ R ters_g(const HotParams<R>& H, R c, R& dg)
 {
     const R q = H.th - c;
     const R iden = Mth<R>::rcp(H.td2 + q * q);
     dg = R(-2) * H.tc2 * q * iden * iden;
-    return R(1) + H.tc2d2 - H.tc2 * iden;
+    return R(1) + H.tc2d2 * q * q * iden;
 }
 
 template <typename R> __device__ __forceinline__ R ters_b(const HotParams<R>& H, R zeta, R& db)
@@ -173,12 +175,4 @@ template <typename R> __device__ __forceinline__ R buck_pair(const HotParams<R>&
     const R S = taper<R>(r, H.b_rt, H.b_rinvw, dS);
     U = V * S;
     return (dV * S + V * dS) * ir;
-}
-
-// Electronic drag coefficient (Sec. 2 "Third"): F_e = -k v with
-// k = gamma (1 + s_loc (rho / rho0 - 1)) inside the target (z >= 0).
-__device__ __forceinline__ double drag_coeff(const DevParams& P, double z, double rho)
-{
-    if (z < 0.0) return 0.0;
-    return P.gamma * (1.0 + P.s_loc * (rho * P.rho0_inv - 1.0));
 }

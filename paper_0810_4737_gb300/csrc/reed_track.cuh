@@ -33,10 +33,15 @@
 enum { SRC_NONE = 0, SRC_PRIMARY = 1, SRC_CLONE = 2 };
 enum { EV_NONE = 0, EV_END = 1, EV_CLONE = 2 };
 
-// Ion state (FP64) as stored in shared memory and in clone records.
-struct IonState {
-    double x[3], v[3], f[3];
-    double rho, t, e_elec, vmax2;
+// Ion state as stored in shared memory and in clone records.  Position,
+// time and the energy given to electronic stopping are FP64 accumulators;
+// velocity, force and the step arithmetic are in the force-pass type R, so
+// the mixed form executes only a handful of FP64 additions per step.
+template <typename R> struct IonState {
+    double x[3];          // absolute position, A
+    double t, e_elec;     // time (tau), energy removed by the drag (eV)
+    R v[3], f[3];         // velocity (A/tau), conservative force (eV/A)
+    R rho, vmax2;         // local density at x; fastest atom's speed^2
     long long steps;
     unsigned long long id, primary, key;
     int A[3];
@@ -44,53 +49,67 @@ struct IonState {
 };
 
 template <typename R> struct TrackShared {
-    IonState ion;
-    double dt;
-    R rel[3];
+    IonState<R> ion;
+    R dt;
+    R rel[3];             // ion position relative to the anchor corner A a
+    R zthr, zback, zsurf; // next cloning depth, backscatter plane, surface in the anchor frame
     int Aold[3];
-    int shift, rebuild, event, status, src, top, nclone, need_count;
+    int shift, rebuild, event, status, src, top, nclone;
+    int need_count, active_count, n_out, out_ovf;
     long long pidx;
     R red[REED_MAX_WARPS][8];
 };
 
 template <typename R> struct V2 { R a, b; };
 
-// Shared-memory carve-up for a window of na atoms.  Tersoff bond data is
-// stored only for "needed" atoms (integrated, or bonded to an integrated
-// atom), at most bond_cap of them, through a compact index need_map.
+// Shared-memory carve-up for a window of na atoms.  Target neighbour lists
+// and Tersoff bond data are kept only for "needed" atoms -- integrated atoms
+// (slots 0 .. active_count-1) and atoms bonded to them -- at most cap of
+// them, addressed through need_map (atom -> slot) and slot_atom.
+#define REED_OUTCAP 64
+
 template <typename R, int TT> struct Layout {
     static __host__ __device__ size_t align(size_t x) { return (x + 15) & ~(size_t)15; }
     static __host__ __device__ size_t shared_bytes() { return align(sizeof(TrackShared<R>)); }
     static __host__ __device__ size_t atoms_bytes(int na) { return 3 * align(sizeof(V4<R>) * na); }
-    static __host__ __device__ size_t nbr_bytes(int na)
+    static __host__ __device__ size_t nbr_bytes(int na, int cap)
     {
-        return TT == REED_TT_NONE ? 0 : align(sizeof(uint16_t) * na * REED_MAXNB) + align(na) +
-                                            align(sizeof(uint16_t) * na);
+        if (TT == REED_TT_NONE) return 0;
+        return align(sizeof(uint16_t) * na) +            // need_map
+               align(na) +                               // flags
+               align(sizeof(uint16_t) * cap) +           // slot_atom
+               align(cap) +                              // nnb
+               align(sizeof(uint16_t) * cap * REED_MAXNB) +  // nbr
+               align(sizeof(uint16_t) * REED_OUTCAP);    // outliers
     }
-    static __host__ __device__ size_t bond_bytes(int bond_cap)
+    static __host__ __device__ size_t bond_bytes(int cap)
     {
-        return TT == REED_TT_TERSOFF ? align(sizeof(V2<R>) * bond_cap * REED_MAXNB) : 0;
+        return TT == REED_TT_TERSOFF ? align(sizeof(V2<R>) * cap * REED_MAXNB) : 0;
     }
-    static __host__ __device__ size_t total(int na, int bond_cap)
+    static __host__ __device__ size_t total(int na, int cap)
     {
-        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na) + bond_bytes(bond_cap);
+        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap) + bond_bytes(cap);
     }
     // bytes of one clone record: ion header + pos, vel, frc
-    static __host__ __device__ size_t entry_bytes(int na) { return align(sizeof(IonState)) + atoms_bytes(na); }
+    static __host__ __device__ size_t entry_bytes(int na) { return align(sizeof(IonState<R>)) + atoms_bytes(na); }
 };
 
 #define REED_NO_SLOT 0xFFFFu
+#define REED_PENDING 0xFFFEu
 
 template <typename R, int TT> struct Win {
     TrackShared<R>* S;
     V4<R>* pos;
     V4<R>* vel;
     V4<R>* frc;
-    uint16_t* nbr;
-    uint8_t* nnb;
-    uint16_t* need_map;
-    V2<R>* bond;
-    __device__ Win(unsigned char* base, int na)
+    uint16_t* need_map;   // atom -> list slot
+    uint8_t* flags;       // bit 0: outlier (far from its home cell)
+    uint16_t* slot_atom;  // list slot -> atom
+    uint8_t* nnb;         // neighbours per slot
+    uint16_t* nbr;        // neighbour atoms per slot
+    uint16_t* outl;       // outlier atoms
+    V2<R>* bond;          // per slot and neighbour: {1/2 dV/db db/dzeta, dV/dr}
+    __device__ Win(unsigned char* base, int na, int cap)
     {
         using L = Layout<R, TT>;
         S = reinterpret_cast<TrackShared<R>*>(base);
@@ -100,17 +119,26 @@ template <typename R, int TT> struct Win {
         vel = reinterpret_cast<V4<R>*>(base + o + ab);
         frc = reinterpret_cast<V4<R>*>(base + o + 2 * ab);
         o += 3 * ab;
-        nbr = nullptr;
-        nnb = nullptr;
         need_map = nullptr;
+        flags = nullptr;
+        slot_atom = nullptr;
+        nnb = nullptr;
+        nbr = nullptr;
+        outl = nullptr;
         bond = nullptr;
         if constexpr (TT != REED_TT_NONE) {
-            nbr = reinterpret_cast<uint16_t*>(base + o);
-            o += L::align(sizeof(uint16_t) * na * REED_MAXNB);
-            nnb = reinterpret_cast<uint8_t*>(base + o);
-            o += L::align(na);
             need_map = reinterpret_cast<uint16_t*>(base + o);
             o += L::align(sizeof(uint16_t) * na);
+            flags = base + o;
+            o += L::align(na);
+            slot_atom = reinterpret_cast<uint16_t*>(base + o);
+            o += L::align(sizeof(uint16_t) * cap);
+            nnb = base + o;
+            o += L::align(cap);
+            nbr = reinterpret_cast<uint16_t*>(base + o);
+            o += L::align(sizeof(uint16_t) * cap * REED_MAXNB);
+            outl = reinterpret_cast<uint16_t*>(base + o);
+            o += L::align(sizeof(uint16_t) * REED_OUTCAP);
         }
         if constexpr (TT == REED_TT_TERSOFF) bond = reinterpret_cast<V2<R>*>(base + o);
     }
@@ -205,210 +233,290 @@ template <typename R> __device__ __forceinline__ bool is_active(const V4<R>& p) 
 template <typename R> __device__ __forceinline__ int species_of(const V4<R>& p) { return ((int)p.w) & 1; }
 
 // ---------------------------------------------------------------------------
-// Target neighbour lists (Tersoff / pair terms): all present atoms within
-// rlist = cutoff + skin (brute force over the window).  nnb[i] holds the
-// count; need_map[i] the compact bond-storage slot of atoms that are
-// integrated or bonded to an integrated atom (REED_NO_SLOT otherwise).
-// Called by all threads right after a barrier.
+// ---------------------------------------------------------------------------
+// Target neighbour lists.  Rebuilt at track start, after a window move and
+// when some atom has travelled more than half the skin since the last build.
+// Candidates of an atom are the atoms of the 27 home cells around its own
+// (the ring layout stores each cell's atoms contiguously) plus the
+// "outliers": atoms more than REED_DISPLACED from their home-cell box, which
+// are checked against everyone.  Two non-outliers closer than rlist always
+// sit in neighbouring home cells because a - 2 REED_DISPLACED > rlist.
+// Integrated atoms get list slots first; atoms bonded to them next.
+// Called by all threads right after a barrier; ends with a barrier.
+// ---------------------------------------------------------------------------
+#define REED_DISPLACED 1.0
+
 template <typename R, int TT>
-__device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow)
+__device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int i, int slot,
+                                      bool brute, int& overflow)
 {
+    const V4<R> pi = W.pos[i];
+    uint16_t* out = W.nbr + (size_t)slot * REED_MAXNB;
+    int cnt = 0;
     const int na = P.na;
-    if (threadIdx.x == 0) W.S->need_count = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < na; i += blockDim.x) {
-        V4<R> pi = W.pos[i];
-        W.need_map[i] = (uint16_t)REED_NO_SLOT;
-        if (!is_present(pi)) {
-            W.nnb[i] = 0;
-            continue;
+    auto consider = [&](int j) {
+        if (j == i) return;
+        const V4<R> pj = W.pos[j];
+        if (!is_present(pj)) return;
+        const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        if (dx * dx + dy * dy + dz * dz < H.rlist2) {
+            if (cnt < REED_MAXNB) out[cnt++] = (uint16_t)j;
+            else ++overflow;
+            if (!is_active(pj) && W.need_map[j] == REED_NO_SLOT) W.need_map[j] = (uint16_t)REED_PENDING;
         }
-        int cnt = 0;
-        bool need = is_active(pi);
-        for (int j = 0; j < na; ++j) {
-            if (j == i) continue;
-            V4<R> pj = W.pos[j];
-            if (!is_present(pj)) continue;
-            R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            R r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < H.rlist2) {
-                if (cnt < REED_MAXNB) {
-                    W.nbr[i * REED_MAXNB + cnt] = (uint16_t)j;
-                    ++cnt;
-                } else {
-                    ++overflow;
+    };
+    if (brute || (W.flags[i] & 1)) {
+        for (int j = 0; j < na; ++j) consider(j);
+    } else {
+        int s[3], b;
+        slot_coords(P, i, s, b);
+        const int n = P.n;
+        const int lo = n >= 3 ? -1 : 0, hi = n >= 3 ? 1 : n - 1;
+        for (int ox = lo; ox <= hi; ++ox) {
+            const int cx = n >= 3 ? pmod(s[0] + ox, n) : ox;
+            for (int oy = lo; oy <= hi; ++oy) {
+                const int cy = n >= 3 ? pmod(s[1] + oy, n) : oy;
+                for (int oz = lo; oz <= hi; ++oz) {
+                    const int cz = n >= 3 ? pmod(s[2] + oz, n) : oz;
+                    const int base = ((cx * n + cy) * n + cz) * P.nb;
+                    for (int q = 0; q < P.nb; ++q)
+                        if (!(W.flags[base + q] & 1)) consider(base + q);
                 }
-                need = need || is_active(pj);
             }
         }
-        W.nnb[i] = (uint8_t)cnt;
-        if (TT == REED_TT_TERSOFF && need) {
-            int slot = atomicAdd(&W.S->need_count, 1);
-            if (slot < P.bond_cap) W.need_map[i] = (uint16_t)slot;
-            else ++overflow;
-        }
-        W.vel[i].w = R(0);   // path length since the list was built
+        const int no = W.S->n_out;
+        for (int k = 0; k < no; ++k) consider(W.outl[k]);
     }
+    return cnt;
 }
 
-// Tersoff pass 1 for atom a: for each bond (a, b) of its list store
-// {pre_ab = 1/2 dV_ab/db * db/dzeta_ab, dV_ab/dr} and return 1/2 sum V_ab.
 template <typename R, int TT>
-__device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int a)
+__device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow,
+                                 int& cap_overflow, bool force_brute = false)
 {
-    const int m = W.nnb[a];
-    V2<R>* bond = W.bond + (size_t)W.need_map[a] * REED_MAXNB;
-    const V4<R> pa = W.pos[a];
-    R dx[REED_MAXNB], dy[REED_MAXNB], dz[REED_MAXNB], r[REED_MAXNB], ir[REED_MAXNB], fc[REED_MAXNB];
-#pragma unroll
-    for (int q = 0; q < REED_MAXNB; ++q) {
-        if (q < m) {
-            V4<R> pb = W.pos[W.nbr[a * REED_MAXNB + q]];
-            dx[q] = pb.x - pa.x;
-            dy[q] = pb.y - pa.y;
-            dz[q] = pb.z - pa.z;
-            R r2 = dx[q] * dx[q] + dy[q] * dy[q] + dz[q] * dz[q];
-            ir[q] = Mth<R>::rsqrt(r2);
-            r[q] = r2 * ir[q];
-            R dfc;
-            fc[q] = ters_fc<R>(H, r[q], dfc);
-        }
+    const int na = P.na;
+    TrackShared<R>* S = W.S;
+    if (threadIdx.x == 0) {
+        S->need_count = 0;
+        S->n_out = 0;
+        S->out_ovf = 0;
     }
-    R E = R(0);
-#pragma unroll
-    for (int q = 0; q < REED_MAXNB; ++q) {
-        if (q < m) {
-            R zeta = R(0);
-#pragma unroll
-            for (int k = 0; k < REED_MAXNB; ++k) {
-                if (k < m && k != q && fc[k] > R(0)) {
-                    R c = (dx[q] * dx[k] + dy[q] * dy[k] + dz[q] * dz[k]) * ir[q] * ir[k];
-                    R dg;
-                    zeta += fc[k] * ters_g<R>(H, c, dg);
+    __syncthreads();
+    // outliers, and list slots for the integrated atoms
+    const R disp = R(REED_DISPLACED);
+    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        const V4<R> p = W.pos[i];
+        uint8_t fl = 0;
+        W.need_map[i] = (uint16_t)REED_NO_SLOT;
+        if (is_present(p)) {
+            int s[3], b;
+            slot_coords(P, i, s, b);
+            const R xs[3] = {p.x, p.y, p.z};
+            for (int d = 0; d < 3; ++d) {
+                const int L = S->ion.A[d] - P.half_n;
+                const R lo = R(L + pmod(s[d] - L, P.n) - S->ion.A[d]) * H.a;
+                if (xs[d] < lo - disp || xs[d] > lo + H.a + disp) fl = 1;
+            }
+            if (fl) {
+                const int k = atomicAdd(&S->n_out, 1);
+                if (k < REED_OUTCAP) W.outl[k] = (uint16_t)i;
+                else S->out_ovf = 1;
+            }
+            if (is_active(p)) {
+                const int slot = atomicAdd(&S->need_count, 1);
+                if (slot < P.bond_cap) {
+                    W.need_map[i] = (uint16_t)slot;
+                    W.slot_atom[slot] = (uint16_t)i;
+                } else {
+                    ++cap_overflow;
                 }
             }
-            R db;
-            R b = ters_b<R>(H, zeta, db);
-            R V, dV, pfa;
-            ters_pair<R>(H, r[q], b, V, dV, pfa);
-            V2<R> out;
-            out.a = R(0.5) * pfa * db;
-            out.b = dV;
-            bond[q] = out;
-            E += R(0.5) * V;
+            W.vel[i].w = R(0);   // path length since the list was built
         }
+        W.flags[i] = fl;
+    }
+    __syncthreads();
+    const bool brute = force_brute || S->out_ovf != 0;
+    if (threadIdx.x == 0) S->active_count = min(S->need_count, P.bond_cap);
+    __syncthreads();
+    // lists of integrated atoms; their other neighbours become pending
+    const int nact = S->active_count;
+    for (int k = threadIdx.x; k < nact; k += blockDim.x) {
+        const int i = W.slot_atom[k];
+        W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, brute, overflow);
+    }
+    __syncthreads();
+    // slots for the pending atoms
+    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        if (W.need_map[i] == REED_PENDING) {
+            const int slot = atomicAdd(&S->need_count, 1);
+            if (slot < P.bond_cap) {
+                W.need_map[i] = (uint16_t)slot;
+                W.slot_atom[slot] = (uint16_t)i;
+            } else {
+                W.need_map[i] = (uint16_t)REED_NO_SLOT;
+                ++cap_overflow;
+            }
+        }
+    }
+    __syncthreads();
+    const int nneed = min(S->need_count, P.bond_cap);
+    for (int k = nact + threadIdx.x; k < nneed; k += blockDim.x) {
+        const int i = W.slot_atom[k];
+        W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, brute, overflow);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) S->need_count = nneed;
+    // (pending marks set by these last lists are not needed: clear them)
+    for (int i = threadIdx.x; i < na; i += blockDim.x)
+        if (W.need_map[i] == REED_PENDING) W.need_map[i] = (uint16_t)REED_NO_SLOT;
+    __syncthreads();
+}
+
+// Tersoff pass 1 for the atom in list slot k: for each bond (a, b) store
+// {pre_ab = 1/2 dV_ab/db * db/dzeta_ab, dV_ab/dr}; returns 1/2 sum_b V_ab.
+template <typename R, int TT>
+__device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned long long& triplets)
+{
+    const int a = W.slot_atom[k];
+    const int m = W.nnb[k];
+    const uint16_t* nb = W.nbr + (size_t)k * REED_MAXNB;
+    V2<R>* bond = W.bond + (size_t)k * REED_MAXNB;
+    const V4<R> pa = W.pos[a];
+    R E = R(0);
+    for (int q = 0; q < m; ++q) {
+        const V4<R> pq = W.pos[nb[q]];
+        const R qx = pq.x - pa.x, qy = pq.y - pa.y, qz = pq.z - pa.z;
+        const R r2q = qx * qx + qy * qy + qz * qz;
+        const R irq = Mth<R>::rsqrt(r2q);
+        const R rq = r2q * irq;
+        R zeta = R(0);
+        for (int p = 0; p < m; ++p) {
+            if (p == q) continue;
+            const V4<R> pk = W.pos[nb[p]];
+            const R kx = pk.x - pa.x, ky = pk.y - pa.y, kz = pk.z - pa.z;
+            const R r2k = kx * kx + ky * ky + kz * kz;
+            const R irk = Mth<R>::rsqrt(r2k);
+            R dfc;
+            const R fck = ters_fc<R>(H, r2k * irk, dfc);
+            if (fck <= R(0)) continue;
+            const R c = (qx * kx + qy * ky + qz * kz) * irq * irk;
+            R dg;
+            zeta += fck * ters_g<R>(H, c, dg);
+            ++triplets;
+        }
+        R db;
+        const R b = ters_b<R>(H, zeta, db);
+        R V, dV, pfa;
+        ters_pair<R>(H, rq, b, V, dV, pfa);
+        V2<R> o;
+        o.a = R(0.5) * pfa * db;
+        o.b = dV;
+        bond[q] = o;
+        E += R(0.5) * V;
     }
     return E;
 }
 
-// Tersoff pass 2: force on atom i gathered from every term of the energy
-// that depends on its position (bonds of i, bonds to i, and bonds of its
-// neighbours in which i is the third atom).
+// Tersoff pass 2: force on integrated atom i (list slot k) gathered from every
+// term of the energy that depends on its position: the bonds of i (radial
+// part and i as the centre of zeta_ib), the bonds (a, i) of its neighbours
+// (radial part and i as the partner in zeta_ai) and the bonds (a, b) in which
+// i is the third atom of zeta_ab.
 template <typename R, int TT>
-__device__ void ters_pass2(const HotParams<R>& H, Win<R, TT>& W, int i, R& Fx, R& Fy, R& Fz)
+__device__ void ters_pass2(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& Fx, R& Fy, R& Fz)
 {
-    const int m = W.nnb[i];
-    if (W.need_map[i] == REED_NO_SLOT) return;
-    const V2<R>* bond_i = W.bond + (size_t)W.need_map[i] * REED_MAXNB;
+    const int m = W.nnb[k];
+    const uint16_t* nb = W.nbr + (size_t)k * REED_MAXNB;
+    const V2<R>* bond_i = W.bond + (size_t)k * REED_MAXNB;
     const V4<R> pi = W.pos[i];
-    R ux[REED_MAXNB], uy[REED_MAXNB], uz[REED_MAXNB], r[REED_MAXNB], fc[REED_MAXNB], dfc[REED_MAXNB];
-#pragma unroll
-    for (int q = 0; q < REED_MAXNB; ++q) {
-        if (q < m) {
-            V4<R> pb = W.pos[W.nbr[i * REED_MAXNB + q]];
-            R dx = pb.x - pi.x, dy = pb.y - pi.y, dz = pb.z - pi.z;
-            R r2 = dx * dx + dy * dy + dz * dz;
-            R irr = Mth<R>::rsqrt(r2);
-            r[q] = r2 * irr;
-            ux[q] = dx * irr;
-            uy[q] = dy * irr;
-            uz[q] = dz * irr;
-            fc[q] = ters_fc<R>(H, r[q], dfc[q]);
-        }
-    }
     R fx = R(0), fy = R(0), fz = R(0);
-    // bonds (i, b): radial part and i as the centre of zeta_ib
-#pragma unroll
-    for (int q = 0; q < REED_MAXNB; ++q) {
-        if (q < m) {
-            V2<R> bq = bond_i[q];
-            R h = R(0.5) * bq.b;
-            fx += h * ux[q];
-            fy += h * uy[q];
-            fz += h * uz[q];
-            R gx = R(0), gy = R(0), gz = R(0);   // d zeta_iq / d x_i
-            if (bq.a != R(0)) {
-#pragma unroll
-                for (int k = 0; k < REED_MAXNB; ++k) {
-                    if (k < m && k != q && (fc[k] > R(0))) {
-                        R c = ux[q] * ux[k] + uy[q] * uy[k] + uz[q] * uz[k];
-                        R dg, g = ters_g<R>(H, c, dg);
-                        R irq = Mth<R>::rcp(r[q]), irk = Mth<R>::rcp(r[k]);
-                        // d c / d x_i = -[(u_k - c u_q)/r_q + (u_q - c u_k)/r_k]
-                        R cx = (ux[k] - c * ux[q]) * irq + (ux[q] - c * ux[k]) * irk;
-                        R cy = (uy[k] - c * uy[q]) * irq + (uy[q] - c * uy[k]) * irk;
-                        R cz = (uz[k] - c * uz[q]) * irq + (uz[q] - c * uz[k]) * irk;
-                        R t = fc[k] * dg;
-                        gx += -dfc[k] * g * ux[k] - t * cx;
-                        gy += -dfc[k] * g * uy[k] - t * cy;
-                        gz += -dfc[k] * g * uz[k] - t * cz;
-                    }
-                }
-                fx -= bq.a * gx;
-                fy -= bq.a * gy;
-                fz -= bq.a * gz;
+    for (int q = 0; q < m; ++q) {
+        const int a = nb[q];
+        const V4<R> pa = W.pos[a];
+        const R dx = pa.x - pi.x, dy = pa.y - pi.y, dz = pa.z - pi.z;
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R ir = Mth<R>::rsqrt(r2);
+        const R ra = r2 * ir;
+        const R ux = dx * ir, uy = dy * ir, uz = dz * ir;   // unit i -> a
+        R dfa;
+        const R fa = ters_fc<R>(H, ra, dfa);
+        const V2<R> bq = bond_i[q];
+        fx += R(0.5) * bq.b * ux;
+        fy += R(0.5) * bq.b * uy;
+        fz += R(0.5) * bq.b * uz;
+        // i as the centre of zeta_ia
+        if (bq.a != R(0)) {
+            R gx = R(0), gy = R(0), gz = R(0);
+            for (int p = 0; p < m; ++p) {
+                if (p == q) continue;
+                const V4<R> pk = W.pos[nb[p]];
+                const R ex = pk.x - pi.x, ey = pk.y - pi.y, ez = pk.z - pi.z;
+                const R r2k = ex * ex + ey * ey + ez * ez;
+                const R irk = Mth<R>::rsqrt(r2k);
+                R dfk;
+                const R fk = ters_fc<R>(H, r2k * irk, dfk);
+                if (fk <= R(0) && dfk == R(0)) continue;
+                const R vx = ex * irk, vy = ey * irk, vz = ez * irk;   // unit i -> k
+                const R c = ux * vx + uy * vy + uz * vz;
+                R dg;
+                const R g = ters_g<R>(H, c, dg);
+                // d c / d x_i = -[(v - c u)/r_a + (u - c v)/r_k]
+                const R cx = (vx - c * ux) * ir + (ux - c * vx) * irk;
+                const R cy = (vy - c * uy) * ir + (uy - c * vy) * irk;
+                const R cz = (vz - c * uz) * ir + (uz - c * vz) * irk;
+                const R t = fk * dg;
+                gx += -dfk * g * vx - t * cx;
+                gy += -dfk * g * vy - t * cy;
+                gz += -dfk * g * vz - t * cz;
             }
+            fx -= bq.a * gx;
+            fy -= bq.a * gy;
+            fz -= bq.a * gz;
         }
-    }
-    // bonds (a, i) and (a, b) for each neighbour a of i
-#pragma unroll
-    for (int q = 0; q < REED_MAXNB; ++q) {
-        if (q < m) {
-            const int a = W.nbr[i * REED_MAXNB + q];
-            const int ma = W.nnb[a];
-            if (W.need_map[a] == REED_NO_SLOT) continue;
-            const V2<R>* bond_a = W.bond + (size_t)W.need_map[a] * REED_MAXNB;
-            const V4<R> pa = W.pos[a];
-            // unit vector a -> i and its length
-            const R vx = -ux[q], vy = -uy[q], vz = -uz[q];
-            const R irai = Mth<R>::rcp(r[q]);
-            R ax = R(0), ay = R(0), az = R(0);   // sum fc(r_ab) g'(c) t  (d zeta_ai / d x_i)
-            R pre_ai = R(0), dV_ai = R(0);
-            for (int p = 0; p < ma; ++p) {
-                const int b = W.nbr[a * REED_MAXNB + p];
-                const V2<R> bab = bond_a[p];
-                if (b == i) {
-                    pre_ai = bab.a;
-                    dV_ai = bab.b;
-                    continue;
-                }
-                const V4<R> pb = W.pos[b];
-                R dx = pb.x - pa.x, dy = pb.y - pa.y, dz = pb.z - pa.z;
-                R r2 = dx * dx + dy * dy + dz * dz;
-                R irab = Mth<R>::rsqrt(r2);
-                R rab = r2 * irab;
-                R wx = dx * irab, wy = dy * irab, wz = dz * irab;
-                R c = vx * wx + vy * wy + vz * wz;
-                R dg, g = ters_g<R>(H, c, dg);
-                R tx = (wx - c * vx) * irai, ty = (wy - c * vy) * irai, tz = (wz - c * vz) * irai;
-                R dfab, fab = ters_fc<R>(H, rab, dfab);
-                ax += fab * dg * tx;
-                ay += fab * dg * ty;
-                az += fab * dg * tz;
-                // i as the third atom of zeta_ab
-                R s1 = dfc[q] * g, s2 = fc[q] * dg;
-                fx -= bab.a * (s1 * vx + s2 * tx);
-                fy -= bab.a * (s1 * vy + s2 * ty);
-                fz -= bab.a * (s1 * vz + s2 * tz);
+        // terms centred on the neighbour a
+        const unsigned sa = W.need_map[a];
+        if (sa >= REED_PENDING) continue;
+        const int ma = W.nnb[sa];
+        const uint16_t* nba = W.nbr + (size_t)sa * REED_MAXNB;
+        const V2<R>* bond_a = W.bond + (size_t)sa * REED_MAXNB;
+        const R vx = -ux, vy = -uy, vz = -uz;   // unit a -> i
+        R ax = R(0), ay = R(0), az = R(0);      // d zeta_ai / d x_i
+        R pre_ai = R(0), dV_ai = R(0);
+        for (int p = 0; p < ma; ++p) {
+            const int b = nba[p];
+            const V2<R> bab = bond_a[p];
+            if (b == i) {
+                pre_ai = bab.a;
+                dV_ai = bab.b;
+                continue;
             }
-            fx -= pre_ai * ax;
-            fy -= pre_ai * ay;
-            fz -= pre_ai * az;
-            R h = R(0.5) * dV_ai;
-            fx += h * ux[q];
-            fy += h * uy[q];
-            fz += h * uz[q];
+            const V4<R> pb = W.pos[b];
+            const R wx0 = pb.x - pa.x, wy0 = pb.y - pa.y, wz0 = pb.z - pa.z;
+            const R r2b = wx0 * wx0 + wy0 * wy0 + wz0 * wz0;
+            const R irb = Mth<R>::rsqrt(r2b);
+            const R wx = wx0 * irb, wy = wy0 * irb, wz = wz0 * irb;   // unit a -> b
+            const R c = vx * wx + vy * wy + vz * wz;
+            R dg;
+            const R g = ters_g<R>(H, c, dg);
+            const R tx = (wx - c * vx) * ir, ty = (wy - c * vy) * ir, tz = (wz - c * vz) * ir;
+            R dfb;
+            const R fb = ters_fc<R>(H, r2b * irb, dfb);
+            ax += fb * dg * tx;
+            ay += fb * dg * ty;
+            az += fb * dg * tz;
+            // i as the third atom of zeta_ab
+            const R s1 = dfa * g, s2 = fa * dg;
+            fx -= bab.a * (s1 * vx + s2 * tx);
+            fy -= bab.a * (s1 * vy + s2 * ty);
+            fz -= bab.a * (s1 * vz + s2 * tz);
         }
+        fx -= pre_ai * ax;
+        fy -= pre_ai * ay;
+        fz -= pre_ai * az;
+        fx += R(0.5) * dV_ai * ux;
+        fy += R(0.5) * dV_ai * uy;
+        fz += R(0.5) * dV_ai * uz;
     }
     Fx += fx;
     Fy += fy;
@@ -418,14 +526,14 @@ __device__ void ters_pass2(const HotParams<R>& H, Win<R, TT>& W, int i, R& Fx, R
 // Buckingham / short-range pair forces on atom i from its list (each pair is
 // visited from both ends; the energy is halved).
 template <typename R, int TT>
-__device__ R pair_force(const HotParams<R>& H, Win<R, TT>& W, int i, R& Fx, R& Fy, R& Fz)
+__device__ R pair_force(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& Fx, R& Fy, R& Fz)
 {
-    const int m = W.nnb[i];
+    const int m = W.nnb[k];
     const V4<R> pi = W.pos[i];
     const int si = species_of(pi);
     R E = R(0);
     for (int q = 0; q < m; ++q) {
-        const V4<R> pj = W.pos[W.nbr[i * REED_MAXNB + q]];
+        const V4<R> pj = W.pos[W.nbr[(size_t)k * REED_MAXNB + q]];
         R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
         R r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= H.b_rc2) continue;
@@ -445,60 +553,90 @@ template <typename R> struct Partial {
     int pairs, bonds;
 };
 
+// Per-thread work counters (algorithmic units of a step, see stats).
+struct WorkCount {
+    unsigned long long triplets = 0;   // Tersoff bond-angle terms (one per zeta term)
+    unsigned long long moved = 0;      // integrated atom updates
+};
+
 // Force evaluation over the whole window; with KICK the second half kick is
 // applied to integrated atoms and their speed^2 reduced for the next dt.
-// Writes W.frc for every present atom.
+// Writes W.frc of every present atom.  With target-target terms the
+// integrated atoms are visited through their list slots (balanced across
+// threads); the others only contribute ion-target pairs.
 template <typename R, int TT, bool KICK>
-__device__ void force_phase(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, R hdt, Partial<R>& out,
-                            bool want_energy)
+__device__ __forceinline__ void atom_force(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int i, int k,
+                                           R hdt, Partial<R>& out, bool want_energy)
 {
     const R ix = W.S->rel[0], iy = W.S->rel[1], iz = W.S->rel[2];
-    for (int i = threadIdx.x; i < P.na; i += blockDim.x) {
-        V4<R> p = W.pos[i];
-        if (!is_present(p)) continue;
-        const bool act = is_active(p);
-        R fx = R(0), fy = R(0), fz = R(0);
-        const R dx = p.x - ix, dy = p.y - iy, dz = p.z - iz;
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < H.rc2) {
-            R U, rw;
-            const R g = ion_pair<R>(H, P.spline_on, P.rho_on, species_of(p), r2, U, rw);
-            fx = -g * dx;
-            fy = -g * dy;
-            fz = -g * dz;
-            out.fx += g * dx;
-            out.fy += g * dy;
-            out.fz += g * dz;
-            out.rho += rw;
-            out.epot += U;
-            out.pairs += 1;
-        }
+    V4<R> p = W.pos[i];
+    const bool act = is_active(p);
+    R fx = R(0), fy = R(0), fz = R(0);
+    const R dx = p.x - ix, dy = p.y - iy, dz = p.z - iz;
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 < H.rc2) {
+        R U, rw;
+        const R g = ion_pair<R>(H, P.spline_on, P.rho_on, species_of(p), r2, U, rw);
+        fx = -g * dx;
+        fy = -g * dy;
+        fz = -g * dz;
+        out.fx += g * dx;
+        out.fy += g * dy;
+        out.fz += g * dz;
+        out.rho += rw;
+        out.epot += U;
+        out.pairs += 1;
+    }
+    if (k >= 0) {
         if constexpr (TT == REED_TT_TERSOFF) {
             if (act) {
-                ters_pass2<R, TT>(H, W, i, fx, fy, fz);
-                out.bonds += W.nnb[i];
+                ters_pass2<R, TT>(H, W, i, k, fx, fy, fz);
+                out.bonds += W.nnb[k];
             }
         }
         if constexpr (TT == REED_TT_BUCKINGHAM) {
             if (act || want_energy) {
-                out.epot += pair_force<R, TT>(H, W, i, fx, fy, fz);
-                out.bonds += W.nnb[i];
+                out.epot += pair_force<R, TT>(H, W, i, k, fx, fy, fz);
+                out.bonds += W.nnb[k];
             }
         }
-        V4<R> f;
-        f.x = fx;
-        f.y = fy;
-        f.z = fz;
-        f.w = R(0);
-        W.frc[i] = f;
-        if (KICK && act) {
-            V4<R> v = W.vel[i];
-            const R k = hdt * H.invM2[species_of(p)];
-            v.x += k * fx;
-            v.y += k * fy;
-            v.z += k * fz;
-            W.vel[i] = v;
-            out.vmax2 = max(out.vmax2, v.x * v.x + v.y * v.y + v.z * v.z);
+    }
+    V4<R> f;
+    f.x = fx;
+    f.y = fy;
+    f.z = fz;
+    f.w = R(0);
+    W.frc[i] = f;
+    if (KICK && act) {
+        V4<R> v = W.vel[i];
+        const R kk = hdt * H.invM2[species_of(p)];
+        v.x += kk * fx;
+        v.y += kk * fy;
+        v.z += kk * fz;
+        W.vel[i] = v;
+        out.vmax2 = max(out.vmax2, v.x * v.x + v.y * v.y + v.z * v.z);
+    }
+}
+
+template <typename R, int TT, bool KICK>
+__device__ void force_phase(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, R hdt, Partial<R>& out,
+                            bool want_energy)
+{
+    if constexpr (TT == REED_TT_NONE) {
+        for (int i = threadIdx.x; i < P.na; i += blockDim.x)
+            if (is_present(W.pos[i])) atom_force<R, TT, KICK>(P, H, W, i, -1, hdt, out, want_energy);
+    } else {
+        // integrated atoms through their slots, then every other present atom
+        const int nact = W.S->active_count;
+        for (int k = threadIdx.x; k < nact; k += blockDim.x)
+            atom_force<R, TT, KICK>(P, H, W, W.slot_atom[k], k, hdt, out, want_energy);
+        for (int i = threadIdx.x; i < P.na; i += blockDim.x) {
+            const V4<R> p = W.pos[i];
+            if (!is_present(p)) continue;
+            const unsigned sl = W.need_map[i];
+            if (is_active(p) && sl < (unsigned)nact) continue;   // done above
+            const int k = (sl < REED_PENDING && want_energy) ? (int)sl : -1;
+            atom_force<R, TT, KICK>(P, H, W, i, k, hdt, out, want_energy);
         }
     }
 }
@@ -520,10 +658,9 @@ __device__ __forceinline__ void reduce_partials(Win<R, TT>& W, Partial<R>& q)
 
 // Sum the per-warp partials (thread 0), fixed order.
 template <typename R, int TT>
-__device__ __forceinline__ void gather_partials(Win<R, TT>& W, double out[8])
+__device__ __forceinline__ void gather_partials(Win<R, TT>& W, R out[8])
 {
     const int nw = (blockDim.x + 31) >> 5;
-    for (int c = 0; c < 8; ++c) out[c] = 0.0;
     R acc[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     for (int w = 0; w < nw; ++w) {
         const R* row = W.S->red[w];
@@ -532,12 +669,12 @@ __device__ __forceinline__ void gather_partials(Win<R, TT>& W, double out[8])
             else acc[c] += row[c];
         }
     }
-    for (int c = 0; c < 8; ++c) out[c] = (double)acc[c];
+    for (int c = 0; c < 8; ++c) out[c] = acc[c];
 }
 
 // Depth bin tally and per-track record of a finished track (Sec. 3: result
 // messages become atomics on device tallies).
-static __device__ void finish_track(const DevParams& P, const DevBuf& B, const IonState& I, int status)
+template <typename R> __device__ void finish_track(const DevParams& P, const DevBuf& B, const IonState<R>& I, int status)
 {
     const double w = ldexp(1.0, -I.level);
     if (status >= REED_TRACK_STOPPED && status <= REED_TRACK_TRUNCATED)
@@ -578,7 +715,7 @@ static __device__ void finish_track(const DevParams& P, const DevBuf& B, const I
 
 // Launch a primary (Sec. 2; lateral position uniform in the (0,0) surface
 // cell, start at z = -rc).
-static __device__ void launch_primary(const DevParams& P, IonState& I, long long pidx)
+template <typename R> __device__ void launch_primary(const DevParams& P, IonState<R>& I, long long pidx)
 {
     I.id = (unsigned long long)(P.first_id + pidx);
     I.primary = I.id;
@@ -587,7 +724,7 @@ static __device__ void launch_primary(const DevParams& P, IonState& I, long long
     draw4(I.key, 0, 0, 0, REED_TAG_LAUNCH, w);
     double th, ph;
     if (P.beam_mode == REED_BEAM_CONE) {
-        double ct = 1.0 - unit_open(w[2]) * (1.0 - P.cos_tmax);
+        const double ct = 1.0 - unit_open(w[2]) * (1.0 - P.cos_tmax);
         th = acos(ct);
         ph = 2.0 * REED_PI * unit_open(w[3]);
     } else {
@@ -597,84 +734,113 @@ static __device__ void launch_primary(const DevParams& P, IonState& I, long long
     I.x[0] = P.a * unit_open(w[0]);
     I.x[1] = P.a * unit_open(w[1]);
     I.x[2] = -P.rc;
-    double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
-    I.v[0] = P.v0 * st * cp;
-    I.v[1] = P.v0 * st * sp;
-    I.v[2] = P.v0 * ct;
-    I.f[0] = I.f[1] = I.f[2] = 0.0;
-    I.rho = 0.0;
+    const double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
+    I.v[0] = R(P.v0 * st * cp);
+    I.v[1] = R(P.v0 * st * sp);
+    I.v[2] = R(P.v0 * ct);
+    I.f[0] = I.f[1] = I.f[2] = R(0);
+    I.rho = R(0);
+    I.vmax2 = R(0);
     I.t = 0.0;
     I.e_elec = 0.0;
-    I.vmax2 = 0.0;
     I.steps = 0;
     I.level = 0;
     for (int d = 0; d < 3; ++d) I.A[d] = (int)floor(I.x[d] / P.a + P.anchor_shift);
 }
 
-template <typename R> __device__ __forceinline__ void set_rel(const DevParams& P, TrackShared<R>* S)
+// Anchor-frame quantities from the FP64 position (track start, window move,
+// cloning): the ion's offset from the anchor corner and the depths that the
+// per-step checks compare against.
+template <typename R> __device__ void set_frame(const DevParams& P, TrackShared<R>* S)
 {
-    for (int d = 0; d < 3; ++d) S->rel[d] = R(S->ion.x[d] - (double)S->ion.A[d] * P.a);
+    const IonState<R>& I = S->ion;
+    for (int d = 0; d < 3; ++d) S->rel[d] = R(I.x[d] - (double)I.A[d] * P.a);
+    const double z0 = (double)I.A[2] * P.a;
+    S->zthr = I.level < P.nthr ? R(P.thr[I.level] - z0) : R(1e30);
+    S->zback = R(-P.rc - z0);
+    S->zsurf = R(-z0);
 }
 
-// Prologue of a step (thread 0): dt, ion half kick + drift, anchor check.
-template <typename R> __device__ void ion_prologue(const DevParams& P, TrackShared<R>* S)
+// Electronic drag coefficient (Sec. 2 "Third"): F_e = -k v with
+// k = gamma (1 + s_loc (rho / rho0 - 1)) inside the target (z >= 0).
+template <typename R> __device__ __forceinline__ R drag_k(const HotParams<R>& H, const TrackShared<R>* S)
 {
-    IonState& I = S->ion;
-    const double v2 = I.v[0] * I.v[0] + I.v[1] * I.v[1] + I.v[2] * I.v[2];
-    const double vmax = sqrt(fmax(v2, I.vmax2));
-    double dt = P.dt_max;
-    if (vmax * dt > P.dx_max) dt = P.dx_max / vmax;
-    const double kd = drag_coeff(P, I.x[2], I.rho);
-    const double h = 0.5 * dt * P.invM1;
+    if (S->rel[2] < S->zsurf) return R(0);
+    return H.gamma * (R(1) + H.s_loc * (S->ion.rho * H.rho0_inv - R(1)));
+}
+
+// Prologue of a step (thread 0): dt from the fastest particle, ion half kick
+// and drift, window anchor check (Fig. "moving cell": the main cell follows
+// the ion).  FP64 work: the position and energy accumulations only.
+template <typename R> __device__ void ion_prologue(const DevParams& P, const HotParams<R>& H, TrackShared<R>* S)
+{
+    IonState<R>& I = S->ion;
+    const R v2 = I.v[0] * I.v[0] + I.v[1] * I.v[1] + I.v[2] * I.v[2];
+    const R vmax = sqrt(max(v2, I.vmax2));
+    R dt = H.dt_max;
+    if (vmax * dt > H.dx_max) dt = H.dx_max / vmax;
+    const R kd = drag_k<R>(H, S);
+    const R h = R(0.5) * dt * H.invM1;
+    R de = R(0);
     for (int d = 0; d < 3; ++d) {
-        const double fe = -kd * I.v[d];
-        I.e_elec -= 0.5 * dt * fe * I.v[d];
+        const R fe = -kd * I.v[d];
+        de -= fe * I.v[d];
         I.v[d] += h * (I.f[d] + fe);
     }
+    I.e_elec += (double)(R(0.5) * dt * de);
     int moved = 0;
     for (int d = 0; d < 3; ++d) {
-        I.x[d] += dt * I.v[d];
-        const int Ad = (int)floor(I.x[d] / P.a + P.anchor_shift);
+        const R dx = dt * I.v[d];
+        I.x[d] += (double)dx;
+        S->rel[d] += dx;
         S->Aold[d] = I.A[d];
-        if (Ad != I.A[d]) moved = 1;
-        I.A[d] = Ad;
+        // the ion leaves its anchor cell when rel leaves [-h a, (1-h) a)
+        if (S->rel[d] >= H.anchor_hi || S->rel[d] < H.anchor_lo) {
+            I.A[d] = (int)floor(I.x[d] / P.a + P.anchor_shift);
+            moved = 1;
+        }
     }
+    if (moved) set_frame<R>(P, S);
     S->shift = moved;
     S->dt = dt;
-    set_rel<R>(P, S);
 }
 
 // Epilogue (thread 0): ion second half kick, end and cloning checks.
 // Returns EV_NONE / EV_END / EV_CLONE; sets S->status and S->nclone.
-template <typename R> __device__ int ion_epilogue(const DevParams& P, TrackShared<R>* S, const double red[8])
+template <typename R>
+__device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShared<R>* S, const R red[8])
 {
-    IonState& I = S->ion;
-    const double dt = S->dt;
+    IonState<R>& I = S->ion;
+    const R dt = S->dt;
     I.f[0] = red[0];
     I.f[1] = red[1];
     I.f[2] = red[2];
     I.rho = red[3];
     I.vmax2 = red[4];
-    const double kd = drag_coeff(P, I.x[2], I.rho);
-    const double h = 0.5 * dt * P.invM1;
+    const R kd = drag_k<R>(H, S);
+    const R h = R(0.5) * dt * H.invM1;
+    R de = R(0);
     for (int d = 0; d < 3; ++d) {
-        const double fe = -kd * I.v[d];
-        I.e_elec -= 0.5 * dt * fe * I.v[d];
+        const R fe = -kd * I.v[d];
+        de -= fe * I.v[d];
         I.v[d] += h * (I.f[d] + fe);
     }
-    I.t += dt;
+    I.e_elec += (double)(R(0.5) * dt * de);
+    I.t += (double)dt;
     I.steps += 1;
-    const double v2 = I.v[0] * I.v[0] + I.v[1] * I.v[1] + I.v[2] * I.v[2];
-    const double E = 0.5 * P.M1 * v2;
+    const R E = R(0.5) * H.M1 * (I.v[0] * I.v[0] + I.v[1] * I.v[1] + I.v[2] * I.v[2]);
     int st = 0;
-    if (!isfinite(E) || !isfinite(I.x[0] + I.x[1] + I.x[2])) st = REED_TRACK_FAILED;
-    else if (E < P.e_stop) st = REED_TRACK_STOPPED;
-    else if (I.x[2] < -P.rc && I.v[2] < 0.0) st = REED_TRACK_BACKSCATTERED;
+    if (!isfinite(E) || !isfinite(S->rel[0] + S->rel[1] + S->rel[2])) st = REED_TRACK_FAILED;
+    else if (E < H.e_stop) st = REED_TRACK_STOPPED;
+    else if (S->rel[2] < S->zback && I.v[2] < R(0)) st = REED_TRACK_BACKSCATTERED;
     else if (I.steps >= P.step_cap) st = REED_TRACK_TRUNCATED;
     S->status = st;
     if (st) return EV_END;
     int nc = 0;
-    while (I.level + nc < P.nthr && I.x[2] >= P.thr[I.level + nc]) ++nc;
+    if (S->rel[2] >= S->zthr) {
+        // passed one (or more) cloning depths: count them on the FP64 depth
+        while (I.level + nc < P.nthr && I.x[2] >= P.thr[I.level + nc]) ++nc;
+    }
     S->nclone = nc;
     return nc ? EV_CLONE : EV_NONE;
 }
@@ -684,7 +850,7 @@ template <typename R, int TT>
 __device__ __forceinline__ void copy_window(const DevParams& P, Win<R, TT>& W, unsigned char* rec, bool to_rec)
 {
     using L = Layout<R, TT>;
-    V4<R>* g = reinterpret_cast<V4<R>*>(rec + L::align(sizeof(IonState)));
+    V4<R>* g = reinterpret_cast<V4<R>*>(rec + L::align(sizeof(IonState<R>)));
     const int na = P.na;
     if (to_rec) {
         for (int i = threadIdx.x; i < na; i += blockDim.x) {
@@ -704,16 +870,15 @@ __device__ __forceinline__ void copy_window(const DevParams& P, Win<R, TT>& W, u
 // Forces + (optionally) target bookkeeping at the start of a track.
 template <typename R, int TT>
 __device__ void initial_forces(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, unsigned long long& ctr_bonds,
-                               unsigned long long& ctr_rebuild, int& nbovf)
+                               unsigned long long& ctr_rebuild, int& nbovf, int& capovf, WorkCount& wc)
 {
     if constexpr (TT != REED_TT_NONE) {
-        build_neighbours<R, TT>(P, H, W, nbovf);
+        build_neighbours<R, TT>(P, H, W, nbovf, capovf);
         if (threadIdx.x == 0) ++ctr_rebuild;
         __syncthreads();
     }
     if constexpr (TT == REED_TT_TERSOFF) {
-        for (int a = threadIdx.x; a < P.na; a += blockDim.x)
-            if (W.need_map[a] != REED_NO_SLOT) ters_pass1<R, TT>(H, W, a);
+        for (int k = threadIdx.x; k < W.S->need_count; k += blockDim.x) ters_pass1<R, TT>(H, W, k, wc.triplets);
         __syncthreads();
     }
     Partial<R> q = {R(0), R(0), R(0), R(0), R(0), R(0), 0, 0};
@@ -721,9 +886,9 @@ __device__ void initial_forces(const DevParams& P, const HotParams<R>& H, Win<R,
     reduce_partials<R, TT>(W, q);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double red[8];
+        R red[8];
         gather_partials<R, TT>(W, red);
-        IonState& I = W.S->ion;
+        IonState<R>& I = W.S->ion;
         I.f[0] = red[0];
         I.f[1] = red[1];
         I.f[2] = red[2];
@@ -741,7 +906,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                                                          const __grid_constant__ DevBuf B)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    Win<R, TT> W(smem, P.na);
+    Win<R, TT> W(smem, P.na, P.bond_cap);
     TrackShared<R>* S = W.S;
     const HotParams<R>& H = hot<R>(P);
     const int tid = threadIdx.x;
@@ -750,7 +915,8 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
     // thread-0 counters, flushed at exit
     unsigned long long c_prim = 0, c_clone = 0, c_tracks = 0, c_steps = 0, c_pairs = 0, c_bonds = 0,
                        c_shift = 0, c_rebuild = 0, c_drop = 0, c_fail = 0;
-    int nbovf = 0;
+    int nbovf = 0, capovf = 0;
+    WorkCount wc;
     if (tid == 0) S->top = 0;
 
     for (;;) {
@@ -770,8 +936,8 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
         if (src == SRC_NONE) break;
         if (src == SRC_PRIMARY) {
             if (tid == 0) {
-                launch_primary(P, S->ion, S->pidx);
-                set_rel<R>(P, S);
+                launch_primary<R>(P, S->ion, S->pidx);
+                set_frame<R>(P, S);
                 ++c_prim;
             }
             __syncthreads();
@@ -786,18 +952,18 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                 W.frc[i] = f;
             }
             __syncthreads();
-            initial_forces<R, TT>(P, H, W, c_bonds, c_rebuild, nbovf);
+            initial_forces<R, TT>(P, H, W, c_bonds, c_rebuild, nbovf, capovf, wc);
         } else {
             unsigned char* rec = stack + (size_t)(S->top - 1) * B.entry_bytes;
             if (tid == 0) {
-                S->ion = *reinterpret_cast<const IonState*>(rec);
-                set_rel<R>(P, S);
+                S->ion = *reinterpret_cast<const IonState<R>*>(rec);
+                set_frame<R>(P, S);
             }
             copy_window<R, TT>(P, W, rec, false);
             __syncthreads();
             if (tid == 0) S->top -= 1;
             if constexpr (TT != REED_TT_NONE) {
-                build_neighbours<R, TT>(P, H, W, nbovf);
+                build_neighbours<R, TT>(P, H, W, nbovf, capovf);
                 if (tid == 0) ++c_rebuild;
             }
             __syncthreads();
@@ -809,7 +975,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
         bool need_prologue = true;
         for (;;) {
             if (need_prologue) {
-                if (tid == 0) ion_prologue<R>(P, S);
+                if (tid == 0) ion_prologue<R>(P, H, S);
                 __syncthreads();
             }
             const R dt = R(S->dt), hdt = R(0.5) * R(S->dt);
@@ -821,6 +987,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                 V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
                 if (shift) any_new |= reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f);
                 if (is_active(p)) {
+                    ++wc.moved;
                     const R k = hdt * H.invM2[species_of(p)];
                     v.x += k * f.x;
                     v.y += k * f.y;
@@ -843,7 +1010,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                 if (tid == 0 && shift) S->rebuild = 1;
                 __syncthreads();
                 if (S->rebuild) {
-                    build_neighbours<R, TT>(P, H, W, nbovf);
+                    build_neighbours<R, TT>(P, H, W, nbovf, capovf);
                     __syncthreads();
                     if (tid == 0) {
                         S->rebuild = 0;
@@ -851,8 +1018,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                     }
                 }
                 if constexpr (TT == REED_TT_TERSOFF) {
-                    for (int a = tid; a < P.na; a += blockDim.x)
-                        if (W.need_map[a] != REED_NO_SLOT) ters_pass1<R, TT>(H, W, a);
+                    for (int k = tid; k < S->need_count; k += blockDim.x) ters_pass1<R, TT>(H, W, k, wc.triplets);
                     __syncthreads();
                 }
             }
@@ -861,15 +1027,15 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             reduce_partials<R, TT>(W, q);
             __syncthreads();
             if (tid == 0) {
-                double red[8];
+                R red[8];
                 gather_partials<R, TT>(W, red);
                 c_pairs += (unsigned long long)red[6];
                 c_bonds += (unsigned long long)red[7];
                 c_shift += shift;
                 ++c_steps;
-                int ev = ion_epilogue<R>(P, S, red);
+                int ev = ion_epilogue<R>(P, H, S, red);
                 if (tracing && S->ion.steps <= P.trace_steps) {
-                    const IonState& I = S->ion;
+                    const IonState<R>& I = S->ion;
                     size_t o = (size_t)pidx * P.trace_steps + (size_t)(I.steps - 1);
                     double* t8 = B.trace + 8 * o;
                     t8[0] = I.x[0]; t8[1] = I.x[1]; t8[2] = I.x[2]; t8[3] = I.t;
@@ -878,7 +1044,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                     a3[0] = I.A[0]; a3[1] = I.A[1]; a3[2] = I.A[2];
                 }
                 S->event = ev;
-                if (ev == EV_NONE) ion_prologue<R>(P, S);
+                if (ev == EV_NONE) ion_prologue<R>(P, H, S);
             }
             __syncthreads();
             const int ev = S->event;
@@ -890,6 +1056,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             if (ev == EV_END) break;
             // ---- cloning (Sec. 2): push one record per level passed
             const int nc = S->nclone;
+            __syncthreads();
             for (int c = 0; c < nc; ++c) {
                 if (S->top >= B.stack_depth || stack == nullptr) {
                     if (tid == 0) {
@@ -902,12 +1069,12 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                 }
                 unsigned char* rec = stack + (size_t)S->top * B.entry_bytes;
                 if (tid == 0) {
-                    IonState& I = S->ion;
+                    IonState<R>& I = S->ion;
                     I.level += 1;
-                    IonState C = I;
+                    IonState<R> C = I;
                     C.id = clone_id(I.id, I.level);
                     C.key = track_key(P.seed, C.id);
-                    *reinterpret_cast<IonState*>(rec) = C;
+                    *reinterpret_cast<IonState<R>*>(rec) = C;
                     ++c_clone;
                 }
                 copy_window<R, TT>(P, W, rec, true);
@@ -915,6 +1082,8 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                 if (tid == 0) S->top += 1;
                 __syncthreads();
             }
+            if (tid == 0) set_frame<R>(P, S);   // next cloning depth
+            __syncthreads();
         }
         // ---- track finished
         if (tid == 0) {
@@ -922,16 +1091,29 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                 ++c_fail;
                 atomicOr(B.status, ERR_NONFINITE);
             }
-            finish_track(P, B, S->ion, S->status);
+            finish_track<R>(P, B, S->ion, S->status);
             ++c_tracks;
         }
         __syncthreads();
     }
-    if (nbovf) atomicOr(B.status, ERR_NEIGHBOR);
+    if (nbovf || capovf) atomicOr(B.status, ERR_NEIGHBOR);
     // flush counters
-    int ov = nbovf;
-    for (int o = 16; o > 0; o >>= 1) ov += __shfl_xor_sync(0xffffffffu, ov, o);
+    int ov = nbovf, oc = capovf;
+    for (int o = 16; o > 0; o >>= 1) {
+        ov += __shfl_xor_sync(0xffffffffu, ov, o);
+        oc += __shfl_xor_sync(0xffffffffu, oc, o);
+    }
     if ((tid & 31) == 0 && ov) atomicAdd(&B.counters[C_NBOVF], (unsigned long long)ov);
+    if ((tid & 31) == 0 && oc) atomicAdd(&B.counters[C_CAPOVF], (unsigned long long)oc);
+    unsigned long long tr = wc.triplets, mv = wc.moved;
+    for (int o = 16; o > 0; o >>= 1) {
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        mv += __shfl_xor_sync(0xffffffffu, mv, o);
+    }
+    if ((tid & 31) == 0) {
+        if (tr) atomicAdd(&B.counters[C_TRIPLETS], tr);
+        atomicAdd(&B.counters[C_MOVED], mv);
+    }
     if (tid == 0) {
         atomicAdd(&B.counters[C_PRIMARIES], c_prim);
         atomicAdd(&B.counters[C_CLONES], c_clone);

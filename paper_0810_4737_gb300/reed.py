@@ -63,7 +63,8 @@ RECORD_DTYPE = np.dtype([("id", "<u8"), ("primary", "<u8"), ("z", "<f8"), ("t", 
 class reed_stats_t(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "primaries", "clones", "tracks", "steps", "pair_evals", "bond_evals", "shifts", "rebuilds",
-        "stopped", "backscattered", "truncated", "failed", "dropped_clones", "nb_overflow")] + \
+        "stopped", "backscattered", "truncated", "failed", "dropped_clones", "nb_overflow", "bond_cap_overflow",
+        "triplets", "atom_updates")] + \
         [("w_stopped", C.c_double), ("w_back", C.c_double), ("w_trunc", C.c_double), ("kernel_ms", C.c_double),
          ("threads_per_track", C.c_int32), ("ctas_per_sm", C.c_int32), ("grid", C.c_int32),
          ("smem_bytes", C.c_int32)]
@@ -287,12 +288,18 @@ class Reed:
         self._sp = species_array(w)
         self.ctx = reed_init(lattice_struct(w), self._sp, len(w["species"]), potentials_struct(w))
 
-    def run(self, n_ions=None, seed=None, precision=PREC_MIXED, **kw):
+    def run(self, n_ions=None, seed=None, precision=PREC_MIXED, tolerate=(), **kw):
+        """Run primaries; anomaly codes listed in `tolerate` (e.g. E_NEIGHBOR)
+        are returned instead of raised (the run is complete, see stats())."""
         w = self.w
         o = run_opts(w, precision=precision, **kw)
         ion = w["ion"]
-        return reed_run(self.ctx, ion["Z"], ion["M"], w["energy"], w["tilt"], w["rot"][0], w["rot"][1],
-                        w["n_ions"] if n_ions is None else n_ions, w["seed"] if seed is None else seed, o)
+        rc = lib().reed_run(self.ctx, ion["Z"], ion["M"], w["energy"], w["tilt"], w["rot"][0], w["rot"][1],
+                            w["n_ions"] if n_ions is None else n_ions, w["seed"] if seed is None else seed,
+                            C.byref(o))
+        if rc < 0 and rc not in tolerate:
+            _check(rc, self.ctx)
+        return rc
 
     def profile(self):
         return reed_range_profile(self.ctx, int(self.w["n_bins"]))

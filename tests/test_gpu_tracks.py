@@ -41,7 +41,8 @@ def _trace_check(R, O, w, n_tracks, n_steps, prec, tol, seed=0, **kw):
         err = np.max(np.abs(traj[t, :k, :3] - ref[:, :3]))
         worst = max(worst, err)
         assert err < tol, (t, err)
-        np.testing.assert_allclose(traj[t, :k, 3], ref[:, 3], rtol=1e-6)
+        # time: dt follows the fastest particle, whose speed is FP32 in the mixed form
+        np.testing.assert_allclose(traj[t, :k, 3], ref[:, 3], rtol=1e-12 if prec == 1 else 2e-5)
         # the window anchor follows the ion identically
         assert np.array_equal(anc[t, :k], ranc)
     return worst

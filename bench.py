@@ -104,10 +104,11 @@ def _ks(a, b):
     return float(stats.ks_2samp(a, b).pvalue)
 
 
-def cpu_baseline(w, n_ions, threads):
-    """The oracle on the host cores, bounded sample; ion-steps/s."""
+def cpu_baseline(w, n_ions, threads, step_cap):
+    """The oracle on the host cores on a bounded sample (n_ions primaries, at
+    most step_cap steps each); ion-steps/s."""
     from oracle import oracle as O
-    p = O.params(w)
+    p = O.params(dict(w, step_cap=step_cap))
     t0 = time.perf_counter()
     r = O.run(p, n_ions, seed=w["seed"], first_id=0, threads=threads, records=False)
     dt = time.perf_counter() - t0
@@ -121,12 +122,12 @@ def run_reference(args):
     from paper_0810_4737_gb300.workloads import workload
     w = workload(args.workload)
     threads = os.cpu_count() or 1
-    n = args.ref_ions
+    n = args.ref_ions or threads
     for _ in range(args.warmup):
-        cpu_baseline(w, max(1, threads // 4), threads)
+        cpu_baseline(w, n, threads, 50)
     vals, steps_tot, t_tot = [], 0, 0.0
     for _ in range(args.steps):
-        v, st, dt = cpu_baseline(w, n, threads)
+        v, st, dt = cpu_baseline(w, n, threads, args.cpu_steps)
         vals.append(v)
         steps_tot += st
         t_tot += dt
@@ -135,9 +136,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "ions_per_step": n, "ion": "As-75", "energy_eV": w["energy"],
-                       "window_atoms": w["n"] ** 3 * 8, "sample": "%d primaries per step" % n},
+                       "window_atoms": w["n"] ** 3 * 8,
+                       "sample": "%d primaries x first %d steps per step" % (n, args.cpu_steps)},
             "cpu_baseline": {"value": value, "unit": "ion-steps/s", "cores": threads, "kind": "oracle",
-                             "sample": "%d primaries of %s per step, FP64 C oracle, OpenMP" % (n, w["name"])},
+                             "sample": "%d primaries of %s, first %d steps each, per step; FP64 C oracle, OpenMP"
+                                       % (n, w["name"], args.cpu_steps)},
             "e2e": {"value": value, "unit": "ion-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -152,8 +155,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--ions", type=int, default=0, help="primaries per step per GPU (0: the workload's)")
     ap.add_argument("--fp64-ions", type=int, default=256, help="sample of the plain FP64 path")
-    ap.add_argument("--cpu-ions", type=int, default=0, help="oracle sample (0: auto, ~10-30 s)")
-    ap.add_argument("--ref-ions", type=int, default=8)
+    ap.add_argument("--cpu-ions", type=int, default=0, help="oracle sample primaries (0: one per host core)")
+    ap.add_argument("--cpu-steps", type=int, default=1200, help="oracle sample: steps per primary")
+    ap.add_argument("--ref-ions", type=int, default=0, help="reference arm primaries per step (0: one per core)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -262,10 +266,11 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         threads = os.cpu_count() or 1
-        ci = args.cpu_ions or max(threads, 16)
-        v, stp, dt = cpu_baseline(w, ci, threads)
+        ci = args.cpu_ions or threads
+        v, stp, dt = cpu_baseline(w, ci, threads, args.cpu_steps)
         cpu = {"value": v, "unit": "ion-steps/s", "cores": threads, "kind": "oracle",
-               "sample": "%d primaries of %s (%d ion-steps, %.1f s), FP64 C oracle with OpenMP" % (ci, w["name"], stp, dt)}
+               "sample": "%d primaries of %s, first %d steps each (%d ion-steps, %.1f s); FP64 C oracle, OpenMP"
+                         % (ci, w["name"], args.cpu_steps, stp, dt)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "ion-steps/s", "n_gpus": ws, "steps": args.steps,
@@ -289,7 +294,7 @@ def main():
             "e2e": e2e,
             "stats": {k: st[k] for k in ("primaries", "tracks", "steps", "pair_evals", "bond_evals", "triplets",
                                          "atom_updates", "shifts", "rebuilds", "nb_overflow", "bond_cap_overflow",
-                                         "threads_per_track", "ctas_per_sm", "grid", "smem_bytes")},
+                                         "threads_per_track", "ctas_per_sm", "grid", "smem_bytes", "phase_cycles")},
         }
         print(json.dumps(line), flush=True)
     ctx.close()

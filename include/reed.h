@@ -156,6 +156,8 @@ typedef struct {
     int64_t bond_cap_overflow; /* atoms left without Tersoff bond storage */
     int64_t triplets;        /* Tersoff bond-angle (zeta) terms evaluated */
     int64_t atom_updates;    /* integrated target-atom updates (atoms x steps) */
+    int64_t phase_cycles[6]; /* SM clock cycles per step phase, summed over CTAs: ion update,
+                                atom move, neighbour build, Tersoff pass 1, forces, track admin */
     double w_stopped, w_back, w_trunc;   /* weights */
     double kernel_ms;        /* device time of the last reed_run */
     int32_t threads_per_track, ctas_per_sm, grid, smem_bytes;  /* last launch */

@@ -539,6 +539,7 @@ int reed_stats(reed_ctx* ctx, reed_stats_t* out)
     out->bond_cap_overflow = (int64_t)c[C_CAPOVF];
     out->triplets = (int64_t)c[C_TRIPLETS];
     out->atom_updates = (int64_t)c[C_MOVED];
+    for (int k = 0; k < REED_NPHASE; ++k) out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
     out->failed = (int64_t)c[C_FAILED];
     out->stopped = (int64_t)c[C_STOP];
     out->backscattered = (int64_t)c[C_BACK];

@@ -25,11 +25,14 @@
 //   -1 for an empty slot (cell above the surface).
 #define REED_W_EMPTY (-1)
 
-enum { REED_NCOUNT = 18 };
+enum { REED_NCOUNT = 24 };
+// cycle counters of the step phases (thread 0 of every CTA, summed)
+enum { PH_ION = 0, PH_MOVE, PH_BUILD, PH_PASS1, PH_FORCE, PH_ADMIN, REED_NPHASE };
+#define C_PHASE0 C_SPARE
 enum {
     C_PRIMARIES = 0, C_CLONES, C_TRACKS, C_STEPS, C_PAIRS, C_BONDS, C_SHIFTS, C_REBUILDS,
     C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_CAPOVF, C_TRIPLETS, C_MOVED, C_SPARE
-};
+};   // C_SPARE .. C_SPARE + REED_NPHASE - 1 hold the phase clocks
 enum { W_STOPPED = 0, W_BACK, W_TRUNC, W_FAILED };
 
 // Hot-loop parameters in the arithmetic type of the force pass (float for

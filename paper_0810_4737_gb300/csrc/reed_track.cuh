@@ -917,6 +917,16 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                        c_shift = 0, c_rebuild = 0, c_drop = 0, c_fail = 0;
     int nbovf = 0, capovf = 0;
     WorkCount wc;
+    // phase clocks (thread 0): time between consecutive barriers of a step
+    unsigned long long ph[REED_NPHASE] = {0, 0, 0, 0, 0, 0};
+    long long t_mark = clock64();
+    auto lap = [&](int phase) {
+        if (tid == 0) {
+            const long long now = clock64();
+            ph[phase] += (unsigned long long)(now - t_mark);
+            t_mark = now;
+        }
+    };
     if (tid == 0) S->top = 0;
 
     for (;;) {
@@ -973,10 +983,12 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
 
         // ---- step loop
         bool need_prologue = true;
+        lap(PH_ADMIN);
         for (;;) {
             if (need_prologue) {
                 if (tid == 0) ion_prologue<R>(P, H, S);
                 __syncthreads();
+                lap(PH_ION);
             }
             const R dt = R(S->dt), hdt = R(0.5) * R(S->dt);
             const int shift = S->shift;
@@ -1009,6 +1021,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             if constexpr (TT != REED_TT_NONE) {
                 if (tid == 0 && shift) S->rebuild = 1;
                 __syncthreads();
+                lap(PH_MOVE);
                 if (S->rebuild) {
                     build_neighbours<R, TT>(P, H, W, nbovf, capovf);
                     __syncthreads();
@@ -1016,16 +1029,19 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                         S->rebuild = 0;
                         ++c_rebuild;
                     }
+                    lap(PH_BUILD);
                 }
                 if constexpr (TT == REED_TT_TERSOFF) {
                     for (int k = tid; k < S->need_count; k += blockDim.x) ters_pass1<R, TT>(H, W, k, wc.triplets);
                     __syncthreads();
+                    lap(PH_PASS1);
                 }
             }
             Partial<R> q = {R(0), R(0), R(0), R(0), R(0), R(0), 0, 0};
             force_phase<R, TT, true>(P, H, W, hdt, q, false);
             reduce_partials<R, TT>(W, q);
             __syncthreads();
+            lap(PH_FORCE);
             if (tid == 0) {
                 R red[8];
                 gather_partials<R, TT>(W, red);
@@ -1047,6 +1063,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                 if (ev == EV_NONE) ion_prologue<R>(P, H, S);
             }
             __syncthreads();
+            lap(PH_ION);
             const int ev = S->event;
             if (ev == EV_NONE) {
                 need_prologue = false;
@@ -1086,6 +1103,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             __syncthreads();
         }
         // ---- track finished
+        lap(PH_ADMIN);
         if (tid == 0) {
             if (S->status == REED_TRACK_FAILED) {
                 ++c_fail;
@@ -1125,5 +1143,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
         atomicAdd(&B.counters[C_REBUILDS], c_rebuild);
         atomicAdd(&B.counters[C_DROPPED], c_drop);
         atomicAdd(&B.counters[C_FAILED], c_fail);
+        lap(PH_ADMIN);
+        for (int k = 0; k < REED_NPHASE; ++k) atomicAdd(&B.counters[C_PHASE0 + k], ph[k]);
     }
 }

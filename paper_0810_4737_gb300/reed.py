@@ -64,13 +64,15 @@ class reed_stats_t(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "primaries", "clones", "tracks", "steps", "pair_evals", "bond_evals", "shifts", "rebuilds",
         "stopped", "backscattered", "truncated", "failed", "dropped_clones", "nb_overflow", "bond_cap_overflow",
-        "triplets", "atom_updates")] + \
+        "triplets", "atom_updates")] + [("phase_cycles", C.c_int64 * 6)] + \
         [("w_stopped", C.c_double), ("w_back", C.c_double), ("w_trunc", C.c_double), ("kernel_ms", C.c_double),
          ("threads_per_track", C.c_int32), ("ctas_per_sm", C.c_int32), ("grid", C.c_int32),
          ("smem_bytes", C.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["phase_cycles"] = list(self.phase_cycles)
+        return d
 
 
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",

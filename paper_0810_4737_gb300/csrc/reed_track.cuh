@@ -56,6 +56,7 @@ template <typename R> struct TrackShared {
     int Aold[3];
     int shift, rebuild, event, status, src, top, nclone;
     int need_count, active_count, n_out, out_ovf;
+    int scan[2][REED_MAX_WARPS];
     long long pidx;
     R red[REED_MAX_WARPS][8];
 };
@@ -290,21 +291,55 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
     return cnt;
 }
 
+// Block-wide exclusive prefix sums of two per-thread counts (threads own
+// contiguous chunks of atoms, so the result follows atom order).  Writes
+// each thread's offsets and returns the totals.  All threads must call it.
+template <typename R>
+__device__ __forceinline__ void block_scan2(TrackShared<R>* S, int c0, int c1, int& o0, int& o1, int& t0, int& t1)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int x0 = c0, x1 = c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+        if (lane >= o) {
+            x0 += y0;
+            x1 += y1;
+        }
+    }
+    __syncthreads();
+    if (lane == 31) {
+        S->scan[0][wid] = x0;
+        S->scan[1][wid] = x1;
+    }
+    __syncthreads();
+    int b0 = 0, b1 = 0;
+    t0 = 0;
+    t1 = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w == wid) {
+            b0 = t0;
+            b1 = t1;
+        }
+        t0 += S->scan[0][w];
+        t1 += S->scan[1][w];
+    }
+    o0 = b0 + x0 - c0;
+    o1 = b1 + x1 - c1;
+}
+
 template <typename R, int TT>
 __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow,
                                  int& cap_overflow, bool force_brute = false)
 {
     const int na = P.na;
     TrackShared<R>* S = W.S;
-    if (threadIdx.x == 0) {
-        S->need_count = 0;
-        S->n_out = 0;
-        S->out_ovf = 0;
-    }
-    __syncthreads();
-    // outliers, and list slots for the integrated atoms
+    const int chunk = (na + blockDim.x - 1) / blockDim.x;
+    const int i0 = min(na, (int)threadIdx.x * chunk), i1 = min(na, i0 + chunk);
+    // outliers and integrated atoms of this thread's chunk
     const R disp = R(REED_DISPLACED);
-    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+    int nout = 0, nact = 0;
+    for (int i = i0; i < i1; ++i) {
         const V4<R> p = W.pos[i];
         uint8_t fl = 0;
         W.need_map[i] = (uint16_t)REED_NO_SLOT;
@@ -317,51 +352,64 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
                 const R lo = R(L + pmod(s[d] - L, P.n) - S->ion.A[d]) * H.a;
                 if (xs[d] < lo - disp || xs[d] > lo + H.a + disp) fl = 1;
             }
-            if (fl) {
-                const int k = atomicAdd(&S->n_out, 1);
-                if (k < REED_OUTCAP) W.outl[k] = (uint16_t)i;
-                else S->out_ovf = 1;
-            }
-            if (is_active(p)) {
-                const int slot = atomicAdd(&S->need_count, 1);
-                if (slot < P.bond_cap) {
-                    W.need_map[i] = (uint16_t)slot;
-                    W.slot_atom[slot] = (uint16_t)i;
-                } else {
-                    ++cap_overflow;
-                }
-            }
+            nout += fl;
+            nact += is_active(p) ? 1 : 0;
             W.vel[i].w = R(0);   // path length since the list was built
         }
         W.flags[i] = fl;
     }
+    int oo, oa, tot_out, tot_act;
+    block_scan2<R>(S, nout, nact, oo, oa, tot_out, tot_act);
+    for (int i = i0; i < i1; ++i) {
+        const V4<R> p = W.pos[i];
+        if (W.flags[i] & 1) {
+            if (oo < REED_OUTCAP) W.outl[oo] = (uint16_t)i;
+            ++oo;
+        }
+        if (is_active(p)) {
+            if (oa < P.bond_cap) {
+                W.need_map[i] = (uint16_t)oa;
+                W.slot_atom[oa] = (uint16_t)i;
+            } else {
+                ++cap_overflow;
+            }
+            ++oa;
+        }
+    }
+    const int nact_slots = min(tot_act, P.bond_cap);
+    if (threadIdx.x == 0) {
+        S->n_out = min(tot_out, REED_OUTCAP);
+        S->out_ovf = tot_out > REED_OUTCAP;
+        S->active_count = nact_slots;
+    }
     __syncthreads();
     const bool brute = force_brute || S->out_ovf != 0;
-    if (threadIdx.x == 0) S->active_count = min(S->need_count, P.bond_cap);
-    __syncthreads();
     // lists of integrated atoms; their other neighbours become pending
-    const int nact = S->active_count;
-    for (int k = threadIdx.x; k < nact; k += blockDim.x) {
+    for (int k = threadIdx.x; k < nact_slots; k += blockDim.x) {
         const int i = W.slot_atom[k];
         W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, brute, overflow);
     }
     __syncthreads();
-    // slots for the pending atoms
-    for (int i = threadIdx.x; i < na; i += blockDim.x) {
-        if (W.need_map[i] == REED_PENDING) {
-            const int slot = atomicAdd(&S->need_count, 1);
-            if (slot < P.bond_cap) {
-                W.need_map[i] = (uint16_t)slot;
-                W.slot_atom[slot] = (uint16_t)i;
-            } else {
-                W.need_map[i] = (uint16_t)REED_NO_SLOT;
-                ++cap_overflow;
-            }
+    // slots for the pending atoms, in atom order after the integrated ones
+    int npend = 0;
+    for (int i = i0; i < i1; ++i) npend += W.need_map[i] == REED_PENDING;
+    int op, dummy, tot_pend, dummy_t;
+    block_scan2<R>(S, npend, 0, op, dummy, tot_pend, dummy_t);
+    op += nact_slots;
+    for (int i = i0; i < i1; ++i) {
+        if (W.need_map[i] != REED_PENDING) continue;
+        if (op < P.bond_cap) {
+            W.need_map[i] = (uint16_t)op;
+            W.slot_atom[op] = (uint16_t)i;
+        } else {
+            W.need_map[i] = (uint16_t)REED_NO_SLOT;
+            ++cap_overflow;
         }
+        ++op;
     }
+    const int nneed = min(nact_slots + tot_pend, P.bond_cap);
     __syncthreads();
-    const int nneed = min(S->need_count, P.bond_cap);
-    for (int k = nact + threadIdx.x; k < nneed; k += blockDim.x) {
+    for (int k = nact_slots + threadIdx.x; k < nneed; k += blockDim.x) {
         const int i = W.slot_atom[k];
         W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, brute, overflow);
     }

@@ -251,6 +251,38 @@ int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double*
                        int32_t* anchors_out, int cap, int32_t* cells_out, int32_t* basis_out,
                        double* xyz_out);
 
+/* ---- a run that allocates no device memory ---------------------------- */
+
+/* reed_run_static: the same track run as reed_run, for callers that cannot
+ * allocate device memory -- for example a host that hands all GPU memory to
+ * its own pool allocator and treats any other cudaMalloc as an error, or a
+ * latency-critical loop that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; it
+ * is an interface convenience.
+ *
+ * No context is needed: the target is described by lat, sp, n_species, pot
+ * (as for reed_init) and the run by the remaining arguments (as for
+ * reed_run).  The launch's scratch (counters, primary queue, status word,
+ * clone stacks) lives in one file-scope device array of 64 MiB that every
+ * GPU loading the library holds until the process exits; the first call on
+ * a device looks up that array's device address, so make the first call
+ * before any stream capture.  Configurations whose clone stacks do not fit
+ * (SMs x n_thresholds x window record) are rejected with REED_E_ARG; the
+ * launch uses fewer CTAs per SM when that makes them fit.  No per-track
+ * records or traces (record_tracks, trace_tracks, trace_steps must be 0).
+ *
+ * hist_out (device, n_bins + 3 doubles) is overwritten with the weighted
+ * range profile followed by {above the surface, beyond the last bin,
+ * backscattered}; stats_out (host, may be NULL) receives the counters.
+ * Every call shares the one scratch array and clears it first, so calls
+ * whose work overlaps on the GPU (from several host threads or streams)
+ * race.  Blocks until the run is finished.  Errors as reed_run;
+ * reed_last_error(NULL) has the message. */
+int reed_run_static(const reed_lattice* lat, const reed_species* sp, int n_species, const reed_potentials* pot,
+                    double ion_Z, double ion_M, double energy_eV, double tilt_deg, double rot_deg_lo,
+                    double rot_deg_hi, int64_t n_ions, uint64_t seed, const reed_run_opts* opt, double* hist_out,
+                    reed_stats_t* stats_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -759,3 +759,196 @@ int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// reed_run_static: a run that allocates no device memory.
+//
+// The scratch of the stepper launch -- work counters, the primary queue head,
+// the status word and the per-CTA clone stacks -- lives in the file-scope
+// array below instead of context buffers.  It is part of this module's
+// image: every GPU that loads the library holds it until the process exits.
+// Host code must not pass the array's name to a kernel (on the host it is
+// only a stand-in for the device copy); the device address is obtained once
+// per device with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define REED_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+#define REED_STATIC_HEADER 4096
+#define REED_STATIC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_reed_static_scratch[REED_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mutex;
+void* g_static_addr[REED_STATIC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device (set-up on the
+// first call for that device).
+int static_scratch(void** out)
+{
+    reed_ctx* ctx = nullptr;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= REED_STATIC_MAX_DEVICES)
+        return fail(nullptr, REED_E_ARG, "reed_run_static: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_reed_static_scratch));
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return REED_OK;
+}
+}  // namespace
+
+extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, int n_species,
+                               const reed_potentials* pot, double ion_Z, double ion_M, double energy_eV,
+                               double tilt_deg, double rot_deg_lo, double rot_deg_hi, int64_t n_ions, uint64_t seed,
+                               const reed_run_opts* opt, double* hist_out, reed_stats_t* stats_out)
+{
+    reed_ctx* ctx = nullptr;   // errors go to the thread's init-error message
+    if (!lat || !sp || !pot || !opt || !hist_out) return fail(nullptr, REED_E_ARG, "reed_run_static: null argument");
+    const reed_run_opts& o = *opt;
+    // the same checks as reed_init and reed_run
+    if (lat->kind != REED_LATTICE_DIAMOND && lat->kind != REED_LATTICE_FLUORITE)
+        return fail(nullptr, REED_E_ARG, "unknown lattice kind %d", lat->kind);
+    if (lat->window_n < 2 || lat->window_n > 6) return fail(nullptr, REED_E_ARG, "window_n must be 2..6");
+    if (lat->frozen_margin < 0 || 2 * lat->frozen_margin >= lat->window_n)
+        return fail(nullptr, REED_E_ARG, "frozen_margin must be 0 or 1 and leave an integrated core");
+    if (!(lat->a > 0.5) || !(lat->sigma >= 0.0)) return fail(nullptr, REED_E_ARG, "invalid lattice constant or sigma");
+    if (n_species != (lat->kind == REED_LATTICE_FLUORITE ? 2 : 1))
+        return fail(nullptr, REED_E_ARG, "wrong number of species");
+    for (int s = 0; s < n_species; ++s)
+        if (!(sp[s].Z > 0) || !(sp[s].M > 0)) return fail(nullptr, REED_E_ARG, "species %d: Z and M must be > 0", s);
+    if (!(pot->rc > 0) || !(pot->r_taper >= 0) || !(pot->r_taper < pot->rc) || !(pot->lam_loc > 0))
+        return fail(nullptr, REED_E_ARG, "invalid ion-target cutoff or density length");
+    if (pot->target_model != REED_TT_NONE && pot->target_model != REED_TT_TERSOFF)
+        return fail(nullptr, REED_E_ARG, "target model %d is not available", pot->target_model);
+    if (pot->target_model == REED_TT_TERSOFF && lat->kind != REED_LATTICE_DIAMOND)
+        return fail(nullptr, REED_E_ARG, "Tersoff needs the one-species diamond lattice");
+    if (!(ion_Z > 0) || !(ion_M > 0) || !(energy_eV > 0) || n_ions < 0)
+        return fail(nullptr, REED_E_ARG, "ion Z, M, energy must be > 0 and n_ions >= 0");
+    if (!(o.dt_max_fs > 0) || !(o.dx_max > 0) || !(o.e_stop >= 0) || o.step_cap < 1)
+        return fail(nullptr, REED_E_ARG, "invalid integrator options");
+    if (o.n_thresholds < 0 || o.n_thresholds > REED_MAX_THR) return fail(nullptr, REED_E_ARG, "n_thresholds must be 0..16");
+    for (int i = 1; i < o.n_thresholds; ++i)
+        if (!(o.thresholds[i] > o.thresholds[i - 1])) return fail(nullptr, REED_E_ARG, "thresholds must ascend");
+    if (o.n_bins < 1 || !(o.bin_width > 0)) return fail(nullptr, REED_E_ARG, "invalid histogram");
+    if (o.beam_mode != REED_BEAM_FIXED && o.beam_mode != REED_BEAM_CONE) return fail(nullptr, REED_E_ARG, "beam_mode");
+    if (o.precision != REED_PREC_MIXED && o.precision != REED_PREC_FP64) return fail(nullptr, REED_E_ARG, "precision");
+    if (o.threads_per_track && !valid_threads(o.threads_per_track))
+        return fail(nullptr, REED_E_ARG, "threads_per_track must be 0, 32, 64, 128 or 256");
+    if (o.ctas_per_sm < 0) return fail(nullptr, REED_E_ARG, "negative ctas_per_sm");
+    if (o.record_tracks || o.trace_tracks || o.trace_steps)
+        return fail(nullptr, REED_E_ARG, "reed_run_static keeps no per-track records or traces");
+
+    // device parameters from a host-only description of the target
+    reed_ctx desc;
+    desc.lat = *lat;
+    desc.nspec = n_species;
+    for (int s = 0; s < n_species; ++s) desc.sp[s] = sp[s];
+    desc.pot = *pot;
+    desc.nbins = o.n_bins;
+    desc.bin_w = o.bin_width;
+    CK(cudaGetDevice(&desc.device));
+    CK(cudaDeviceGetAttribute(&desc.sms, cudaDevAttrMultiProcessorCount, desc.device));
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, desc.device));
+    DevParams P;
+    make_params(&desc, P, ion_Z, ion_M, energy_eV, tilt_deg, rot_deg_lo, rot_deg_hi, o);
+    P.seed = seed;
+    P.n_primaries = n_ions;
+    P.record = 0;
+    P.trace_tracks = 0;
+    P.trace_steps = 0;
+
+    const int tt = P.tt;
+    const bool f64 = o.precision == REED_PREC_FP64;
+    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap) : reed_f32::smem_bytes(tt, P.na, P.bond_cap);
+    if (smem > (size_t)optin)
+        return fail(nullptr, REED_E_SMEM, "window of %d atoms needs %zu B of shared memory (max %d)", P.na, smem, optin);
+    LaunchCfg L;
+    L.threads = o.threads_per_track ? o.threads_per_track : (tt == REED_TT_NONE ? 64 : 256);
+    L.smem = smem;
+    int occ = 0;
+    CK(f64 ? reed_f64::occupancy(tt, L.threads, smem, &occ) : reed_f32::occupancy(tt, L.threads, smem, &occ));
+    if (occ < 1) return fail(nullptr, REED_E_SMEM, "kernel does not fit on an SM");
+    L.ctas_per_sm = o.ctas_per_sm ? std::min(o.ctas_per_sm, occ) : occ;
+
+    // clone stacks must fit in the static scratch: fewer CTAs per SM if needed
+    DevBuf B;
+    std::memset(&B, 0, sizeof(B));
+    B.entry_bytes = f64 ? reed_f64::entry_bytes(tt, P.na) : reed_f32::entry_bytes(tt, P.na);
+    B.stack_depth = P.nthr;
+    B.stack_stride = B.entry_bytes * (size_t)std::max(P.nthr, 1);
+    const size_t room = REED_STATIC_SCRATCH_BYTES - REED_STATIC_HEADER;
+    if (P.nthr > 0) {
+        while (L.ctas_per_sm > 1 && B.stack_stride * (size_t)desc.sms * L.ctas_per_sm > room) --L.ctas_per_sm;
+        if (B.stack_stride * (size_t)desc.sms * L.ctas_per_sm > room)
+            return fail(nullptr, REED_E_ARG,
+                        "clone stacks need %zu B (%d SMs x %d levels x %zu B), more than the %zu B static scratch",
+                        B.stack_stride * (size_t)desc.sms, desc.sms, P.nthr, B.entry_bytes, room);
+    }
+    L.grid = desc.sms * L.ctas_per_sm;
+
+    unsigned char* base = nullptr;
+    int rc = static_scratch((void**)&base);
+    if (rc) return rc;
+    B.counters = reinterpret_cast<unsigned long long*>(base);
+    B.wsum = reinterpret_cast<double*>(base + 256);
+    B.next = reinterpret_cast<unsigned long long*>(base + 512);
+    B.status = reinterpret_cast<int*>(base + 768);
+    B.record_count = reinterpret_cast<unsigned long long*>(base + 1024);
+    B.stacks = P.nthr > 0 ? base + REED_STATIC_HEADER : nullptr;
+    B.hist = hist_out;
+    B.records = nullptr;
+    B.trace = nullptr;
+    B.trace_anchor = nullptr;
+
+    cudaStream_t st = (cudaStream_t)o.stream;
+    // the array keeps the previous call's contents: clear what must start at zero
+    CK(cudaMemsetAsync(base, 0, REED_STATIC_HEADER, st));
+    CK(cudaMemsetAsync(hist_out, 0, sizeof(double) * (o.n_bins + 3), st));
+    if (n_ions > 0) CK(f64 ? reed_f64::launch_track(tt, P, B, L, st) : reed_f32::launch_track(tt, P, B, L, st));
+    CK(cudaStreamSynchronize(st));
+    unsigned long long c[REED_NCOUNT];
+    double w[4];
+    int status = 0;
+    CK(cudaMemcpy(c, B.counters, sizeof(c), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(w, B.wsum, sizeof(w), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&status, B.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (stats_out) {
+        std::memset(stats_out, 0, sizeof(*stats_out));
+        stats_out->primaries = (int64_t)c[C_PRIMARIES];
+        stats_out->clones = (int64_t)c[C_CLONES];
+        stats_out->tracks = (int64_t)c[C_TRACKS];
+        stats_out->steps = (int64_t)c[C_STEPS];
+        stats_out->pair_evals = (int64_t)c[C_PAIRS];
+        stats_out->bond_evals = (int64_t)c[C_BONDS];
+        stats_out->shifts = (int64_t)c[C_SHIFTS];
+        stats_out->rebuilds = (int64_t)c[C_REBUILDS];
+        stats_out->dropped_clones = (int64_t)c[C_DROPPED];
+        stats_out->nb_overflow = (int64_t)c[C_NBOVF];
+        stats_out->bond_cap_overflow = (int64_t)c[C_CAPOVF];
+        stats_out->failed = (int64_t)c[C_FAILED];
+        stats_out->stopped = (int64_t)c[C_STOP];
+        stats_out->backscattered = (int64_t)c[C_BACK];
+        stats_out->truncated = (int64_t)c[C_TRUNC];
+        stats_out->triplets = (int64_t)c[C_TRIPLETS];
+        stats_out->atom_updates = (int64_t)c[C_MOVED];
+        for (int k = 0; k < REED_NPHASE; ++k) stats_out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
+        stats_out->w_stopped = w[W_STOPPED];
+        stats_out->w_back = w[W_BACK];
+        stats_out->w_trunc = w[W_TRUNC];
+        stats_out->threads_per_track = L.threads;
+        stats_out->ctas_per_sm = L.ctas_per_sm;
+        stats_out->grid = L.grid;
+        stats_out->smem_bytes = (int32_t)L.smem;
+    }
+    if (status & ERR_NONFINITE) return fail(nullptr, REED_E_NONFINITE, "a track became non-finite");
+    if (status & ERR_QUEUE) return fail(nullptr, REED_E_QUEUE_FULL, "clone stack overflow: clones dropped");
+    if (status & ERR_NEIGHBOR) return fail(nullptr, REED_E_NEIGHBOR, "neighbour list overflow");
+    return REED_OK;
+}

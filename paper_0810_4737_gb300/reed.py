@@ -77,7 +77,7 @@ class reed_stats_t(C.Structure):
 
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",
             "reed_reset", "reed_last_error", "reed_destroy", "reed_philox", "reed_cell_atoms", "reed_forces",
-            "reed_window_replay"]
+            "reed_window_replay", "reed_run_static"]
 
 _LIB = None
 _D = C.POINTER(C.c_double)
@@ -121,6 +121,10 @@ def lib():
         L.reed_cell_atoms.argtypes = [vp, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, _D, _I32]
         L.reed_forces.argtypes = [vp, C.c_int, C.c_double, C.c_double, _D, C.c_int, _D, _I32, _D, _D, _D, _D]
         L.reed_window_replay.argtypes = [vp, C.c_int, C.c_uint64, _D, C.c_int, _I32, C.c_int, _I32, _I32, _D]
+        L.reed_run_static.argtypes = [C.POINTER(reed_lattice), C.POINTER(reed_species), C.c_int,
+                                      C.POINTER(reed_potentials), C.c_double, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_double, C.c_int64, C.c_uint64, C.POINTER(reed_run_opts), vp,
+                                      C.POINTER(reed_stats_t)]
         _LIB = L
     return _LIB
 
@@ -280,6 +284,20 @@ def reed_window_replay(ctx, precision, key, path, cap=2000):
                                         bas.ctypes.data_as(_I32), xyz.ctypes.data_as(_D)), ctx)
     m = min(n, cap)
     return anc, cells[:m].copy(), bas[:m].copy(), xyz[:m].copy()
+
+
+def reed_run_static(w, n_ions, seed, hist_out_ptr, precision=PREC_MIXED, stream=None, **kw):
+    """Run without any device allocation (see include/reed.h): the workload
+    dict describes target and run; hist_out_ptr is a device buffer of
+    n_bins + 3 doubles owned by the caller.  Returns the stats dict."""
+    sp = species_array(w)
+    o = run_opts(w, precision=precision, record=False, stream=stream, **kw)
+    st = reed_stats_t()
+    ion = w["ion"]
+    _check(lib().reed_run_static(C.byref(lattice_struct(w)), sp, len(w["species"]), C.byref(potentials_struct(w)),
+                                 ion["Z"], ion["M"], w["energy"], w["tilt"], w["rot"][0], w["rot"][1], n_ions, seed,
+                                 C.byref(o), hist_out_ptr, C.byref(st)))
+    return st.as_dict()
 
 
 class Reed:

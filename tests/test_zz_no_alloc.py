@@ -1,0 +1,80 @@
+"""reed_run_static: the run entry point that allocates no device memory.
+
+Some callers cannot allocate GPU memory themselves -- their host owns all
+device memory through its own pool, or cannot pay cudaMalloc's implicit
+synchronisation -- so the library offers one entry point whose launch
+scratch lives in a fixed file-scope device array.  These tests call it
+through the C ABI and check that it reproduces the context-based entry
+point (reed_run + reed_range_profile) exactly, on two calls in a row (the
+shared scratch must not leak one call's state into the next), and that a
+configuration too large for the fixed scratch is refused.
+
+This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_0810_4737_gb300.workloads import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_0810_4737_gb300 import build, reed
+    build.build()
+    return reed
+
+
+def _reference(R, w, n, seed, prec):
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n, seed=seed, precision=prec)
+        bins, extra = ctx.profile()
+        st = ctx.stats()
+    return np.concatenate([bins, extra]), st
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_static_run_matches_the_context_run(R, prec):
+    import torch
+    # thermal Si with rare-event cloning: exercises the clone stacks in the scratch
+    w = workload("b1kev_si_0k_zbl", sigma=0.076, rot=(0.0, 45.0), energy=2000.0,
+                 thresholds=[40.0, 70.0, 110.0, 160.0])
+    n, nb = 512, int(w["n_bins"]) + 3
+    out = torch.full((nb,), -1.0, dtype=torch.float64, device="cuda")   # caller-owned output
+    for seed in (11, 11, 12):          # two identical calls in a row, then another seed
+        st = R.reed_run_static(w, n, seed, out.data_ptr(), precision=prec)
+        got = out.cpu().numpy()
+        ref, rst = _reference(R, w, n, seed, prec)
+        np.testing.assert_allclose(got, ref, rtol=0, atol=0)   # weights 2^-k: sums are exact
+        for k in ("primaries", "clones", "tracks", "steps", "stopped", "backscattered", "truncated"):
+            assert st[k] == rst[k], k
+        assert got.sum() == n
+
+
+def test_static_run_tersoff_matches(R):
+    import torch
+    w = workload("as10kev_si_300k_tersoff", energy=2000.0)
+    n, nb = 64, int(w["n_bins"]) + 3
+    out = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        st = R.reed_run_static(w, n, 5, out.data_ptr())
+        ref, rst = _reference(R, w, n, 5, 0)
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=0)
+        assert st["steps"] == rst["steps"]
+
+
+def test_static_run_refuses_oversized_scratch(R):
+    import torch
+    # FP64 1000-atom windows with 16 cloning levels need ~0.2 GB of stacks
+    w = workload("as10kev_si_300k_tersoff", thresholds=[100.0 * (k + 1) for k in range(16)])
+    out = torch.zeros(int(w["n_bins"]) + 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(R.ReedError) as e:
+        R.reed_run_static(w, 4, 0, out.data_ptr(), precision=R.PREC_FP64)
+    assert e.value.code == R.E_ARG and "static scratch" in str(e.value)
+    # records are not available without allocation
+    with pytest.raises(R.ReedError):
+        o = R.run_opts(w, record=True)
+        sp = R.species_array(w)
+        R._check(R.lib().reed_run_static(R.C.byref(R.lattice_struct(w)), sp, 1, R.C.byref(R.potentials_struct(w)),
+                                         33.0, 74.9, 1e4, 7.0, 0.0, 45.0, 1, 0, R.C.byref(o), out.data_ptr(), None))

@@ -185,8 +185,7 @@ def main():
     first = rank * 10_000_000
 
     def one(step_idx, record=False):
-        return ctx.run(n_ions=n, seed=w["seed"], first_id=first + step_idx * n, record=record, stream=sh,
-                       tolerate=(R.E_NEIGHBOR,))
+        return ctx.run(n_ions=n, seed=w["seed"], first_id=first + step_idx * n, record=record, stream=sh)
 
     for i in range(args.warmup):
         one(i)
@@ -234,7 +233,7 @@ def main():
         t0 = time.perf_counter()
         e2e_steps = 0
         for i in range(args.steps):
-            ctx.run(n_ions=n, seed=w["seed"], first_id=first + (100 + i) * n, record=False, tolerate=(R.E_NEIGHBOR,))
+            ctx.run(n_ions=n, seed=w["seed"], first_id=first + (100 + i) * n, record=False)
             bins, extra = ctx.profile()                 # device -> host
             e2e_steps = ctx.stats()["steps"]            # device -> host
         dt = time.perf_counter() - t0
@@ -248,12 +247,10 @@ def main():
     if rank == 0 and args.fp64_ions > 0:
         m = args.fp64_ions
         with R.Reed(w) as c64, R.Reed(w) as c32:
-            c64.run(n_ions=m, seed=w["seed"], first_id=first, precision=R.PREC_FP64, stream=sh,
-                    tolerate=(R.E_NEIGHBOR,))
+            c64.run(n_ions=m, seed=w["seed"], first_id=first, precision=R.PREC_FP64, stream=sh)
             s64 = c64.stats()
             r64 = c64.records()
-            c32.run(n_ions=m, seed=w["seed"], first_id=first, precision=R.PREC_MIXED, stream=sh,
-                    tolerate=(R.E_NEIGHBOR,))
+            c32.run(n_ions=m, seed=w["seed"], first_id=first, precision=R.PREC_MIXED, stream=sh)
             s32 = c32.stats()
             r32 = c32.records()
         z64 = r64["z"][r64["status"] == R.STOPPED]

@@ -47,7 +47,10 @@ extern "C" {
 #define REED_E_NOMEM -6      /* device memory allocation failed */
 #define REED_E_SMEM -7       /* the window does not fit in shared memory */
 #define REED_E_STATE -8      /* call made in the wrong state (e.g. no run yet) */
-#define REED_E_NEIGHBOR -9   /* target neighbour list overflowed (forces truncated) */
+#define REED_E_NEIGHBOR -9   /* (reserved) */
+/* Positive codes: the run completed, with a counted anomaly (see reed_stats). */
+#define REED_W_NEIGHBOR 1    /* some atom had more target neighbours than a list holds: the
+                                surplus bonds were left out of its forces (nb_overflow) */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define REED_LATTICE_DIAMOND 0   /* 8-atom cubic cell, one species (Si) */
@@ -182,9 +185,11 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
  * and track id).  Blocks until the run is finished.  opt may be NULL (all
  * defaults: 0.1 fs, 0.05 A, 5 eV, 2e6 steps, mixed precision, no cloning,
  * 100 bins of 10 A).  With record_tracks and record_capacity 0 the record
- * buffer holds n_ions * (1 + 4 n_thresholds) + 1024 records.  Errors: REED_E_ARG, REED_E_SMEM, REED_E_CUDA,
- * REED_E_NOMEM; REED_E_QUEUE_FULL / REED_E_NONFINITE / REED_E_NEIGHBOR report
- * anomalies counted in reed_stats (the run still completes). */
+ * buffer holds n_ions * (1 + 4 n_thresholds) + 1024 records.
+ * Returns REED_OK, REED_W_NEIGHBOR (completed; see nb_overflow), or an error:
+ * REED_E_ARG, REED_E_SMEM, REED_E_CUDA, REED_E_NOMEM; REED_E_QUEUE_FULL and
+ * REED_E_NONFINITE mean the run completed but clones or tracks were lost
+ * (counted in reed_stats). */
 int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double tilt_deg,
              double rot_deg_lo, double rot_deg_hi, int64_t n_ions, uint64_t seed,
              const reed_run_opts* opt);
@@ -276,7 +281,7 @@ int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double*
  * backscattered}; stats_out (host, may be NULL) receives the counters.
  * Every call shares the one scratch array and clears it first, so calls
  * whose work overlaps on the GPU (from several host threads or streams)
- * race.  Blocks until the run is finished.  Errors as reed_run;
+ * race.  Blocks until the run is finished.  Returns as reed_run;
  * reed_last_error(NULL) has the message. */
 int reed_run_static(const reed_lattice* lat, const reed_species* sp, int n_species, const reed_potentials* pot,
                     double ion_Z, double ion_M, double energy_eV, double tilt_deg, double rot_deg_lo,

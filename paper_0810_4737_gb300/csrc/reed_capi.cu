@@ -504,7 +504,10 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     CK(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (status & ERR_NONFINITE) return fail(ctx, REED_E_NONFINITE, "a track became non-finite (see reed_stats)");
     if (status & ERR_QUEUE) return fail(ctx, REED_E_QUEUE_FULL, "clone stack overflow: clones dropped");
-    if (status & ERR_NEIGHBOR) return fail(ctx, REED_E_NEIGHBOR, "neighbour list overflow (see reed_stats)");
+    if (status & ERR_NEIGHBOR) {
+        fail(ctx, REED_W_NEIGHBOR, "neighbour lists truncated (see nb_overflow in reed_stats)");
+        return REED_W_NEIGHBOR;
+    }
     return REED_OK;
 }
 
@@ -949,6 +952,9 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     }
     if (status & ERR_NONFINITE) return fail(nullptr, REED_E_NONFINITE, "a track became non-finite");
     if (status & ERR_QUEUE) return fail(nullptr, REED_E_QUEUE_FULL, "clone stack overflow: clones dropped");
-    if (status & ERR_NEIGHBOR) return fail(nullptr, REED_E_NEIGHBOR, "neighbour list overflow");
+    if (status & ERR_NEIGHBOR) {
+        fail(nullptr, REED_W_NEIGHBOR, "neighbour lists truncated (see nb_overflow)");
+        return REED_W_NEIGHBOR;
+    }
     return REED_OK;
 }

@@ -16,6 +16,7 @@ from . import build as _build
 
 OK = 0
 E_ARG, E_CUDA, E_TIMEOUT, E_QUEUE_FULL, E_NONFINITE, E_NOMEM, E_SMEM, E_STATE, E_NEIGHBOR = range(-1, -10, -1)
+W_NEIGHBOR = 1   # completed; some neighbour lists were truncated (stats["nb_overflow"])
 LATTICE = {"diamond": 0, "fluorite": 1}
 TT = {"none": 0, "tersoff": 1, "buckingham": 2}
 PREC_MIXED, PREC_FP64 = 0, 1

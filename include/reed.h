@@ -133,6 +133,22 @@ typedef struct {
     int32_t reserved;
     int64_t record_capacity;   /* records kept (further tracks are counted only) */
     void* stream;              /* cudaStream_t to run on; NULL = default stream */
+    /* Adaptive cloning depths (Sec. 2; re-estimated from finished ions, Sec. 3):
+     * with adaptive = 1 the first n_initial primaries run without enhancement,
+     * then the run proceeds in epochs of epoch_size primaries; before each
+     * epoch the n_thresholds depths are re-estimated on the device as
+     * d_k = S^-1(2^-k), S(d) = weighted fraction of finished tracks stopped at
+     * depth >= d (linear interpolation in the range histogram; +inf when the
+     * target lies beyond it).  With n_initial = 0 the first epoch uses
+     * thresholds[] as the initial guess.  A track never sees its depths change. */
+    int32_t adaptive;
+    int32_t reserved2;
+    int64_t epoch_size;        /* primaries per epoch (adaptive) */
+    int64_t n_initial;         /* unenhanced primaries before the first epoch (adaptive) */
+    /* Stop handing out primaries once this many tracks (clones included) have
+     * finished; tracks already running are completed (the paper's kill
+     * signal, Sec. 3).  0 = run all n_ions. */
+    int64_t target_tracks;
 } reed_run_opts;
 
 /* Per-track result: the depth and weight of one finished track (Sec. 3, result messages). */
@@ -214,6 +230,12 @@ int reed_track_records(reed_ctx* ctx, reed_track_record* out, int64_t cap, int64
  * (x y z t vx vy vz dt; steps after a track ended are zero), anchors (host or
  * device, may be NULL) 3 int32 window anchor indices per step. */
 int reed_trace(reed_ctx* ctx, double* traj, int32_t* anchors, int n_tracks, int n_steps);
+
+/* Cloning depths used by the enhanced epochs of the last adaptive run (the
+ * evolution of cloning points, Sec. 4.1): history (host or device) receives up
+ * to max_epochs rows of 16 doubles (first n_thresholds valid, +inf = no
+ * depth); *n_epochs (host) the number of enhanced epochs run. */
+int reed_thresholds(reed_ctx* ctx, double* history, int max_epochs, int* n_epochs);
 
 /* Zero all tallies, records and counters. */
 int reed_reset(reed_ctx* ctx);

@@ -112,6 +112,11 @@ def lib():
                                         C.c_double, _D]
             L.o_md_explicit.restype = C.c_int
             L.o_launch_state.argtypes = [_P, C.c_uint64, C.c_uint64, _D, _D]
+            L.o_update_thresholds.argtypes = [_D, C.c_int, C.c_double, C.c_int, _D]
+            L.o_update_thresholds.restype = C.c_int
+            L.o_run_adaptive.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_uint64, C.c_int, _D,
+                                         C.POINTER(C.c_int64), _D, _D, C.c_int]
+            L.o_run_adaptive.restype = C.c_int
             L.o_basis_count.argtypes = [C.c_int]
             L.o_basis_count.restype = C.c_int
             _LIB = L
@@ -313,3 +318,29 @@ def md_explicit(p: Params, ion_x, ion_v, x, v, sp, act=None, nsteps=1000, dt_fix
     k = lib().o_md_explicit(C.byref(p), _dp(xi), _dp(vi), xa.shape[0], _dp(xa), _dp(va), _ip(s), _ip(a),
                             nsteps, dt_fixed, stop_sep, _dp(E) if energies else None)
     return xi, vi, xa, va, k, (E[:k + 1] if energies else None)
+
+
+def update_thresholds(hist_full, bin_w, nthr):
+    """Cloning depths d_k = S^-1(2^-k) from a histogram of nbins + 3 entries."""
+    h = np.ascontiguousarray(hist_full, dtype=np.float64)
+    out = np.zeros(max(nthr, 1))
+    rc = lib().o_update_thresholds(_dp(h), h.size - 3, bin_w, nthr, _dp(out))
+    if rc != 0:
+        raise ValueError("empty histogram")
+    return out[:nthr].copy()
+
+
+def run_adaptive(p: Params, n_ions: int, n_initial: int, epoch: int, seed: int, threads: int | None = None,
+                 max_epochs: int = 256):
+    """Adaptive-depth run (see o_run_adaptive); returns the histogram dict and
+    the depths used by each enhanced epoch."""
+    nb = p.nbins + 3
+    hist = np.zeros(nb)
+    cnt = np.zeros(4, dtype=np.int64)
+    wt = np.zeros(1)
+    th = np.zeros((max_epochs, 16))
+    ne = lib().o_run_adaptive(C.byref(p), n_ions, n_initial, epoch, seed, threads or (os.cpu_count() or 1),
+                              _dp(hist), cnt.ctypes.data_as(C.POINTER(C.c_int64)), _dp(wt), _dp(th), max_epochs)
+    return {"hist": hist[:p.nbins].copy(), "under": hist[p.nbins], "over": hist[p.nbins + 1],
+            "back": hist[p.nbins + 2], "w_trunc": wt[0], "steps": int(cnt[0]), "tracks": int(cnt[1]),
+            "clones": int(cnt[2]), "thresholds": th[:min(ne, max_epochs), :p.nthr].copy(), "epochs": ne}

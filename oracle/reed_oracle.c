@@ -1070,6 +1070,83 @@ int o_md_explicit(const o_params* P, double* ion_x, double* ion_v, int n, double
 
 void o_free(void* p) { free(p); }
 
+/* ------------------------------------------------------------------------ */
+/* Adaptive cloning depths (Sec. 2: depths chosen so that every interval    */
+/* between them collects a similar count; re-estimated from all finished    */
+/* ions, Sec. 3).  reading: with weights 2^-k the count between d_k and      */
+/* d_{k+1} is equal when S(d_k) = 2^-k, S(d) = weighted fraction of          */
+/* finished tracks that stopped at depth >= d (backscattered and above-      */
+/* surface tracks count as not reaching any d > 0).  S is read off the       */
+/* depth histogram with linear interpolation inside a bin.  Targets beyond   */
+/* the histogram's last bin give depth +inf (no cloning at that level).      */
+/* hist has nbins + 3 entries (under, over, back appended).                  */
+/* ------------------------------------------------------------------------ */
+int o_update_thresholds(const double* hist, int nbins, double bin_w, int nthr, double* thr)
+{
+    double total = 0.0;
+    for (int b = 0; b < nbins + 3; ++b) total += hist[b];
+    if (!(total > 0.0)) return -1;
+    double over = hist[nbins + 1];
+    for (int k = 1; k <= nthr; ++k) {
+        double target = ldexp(total, -k);   /* weight that must lie at or beyond d_k */
+        double d = INFINITY;
+        if (over < target) {
+            /* walk the bins from the deep end: tail(b) = weight at depth >= b*w */
+            double tail = over;
+            for (int b = nbins - 1; b >= 0; --b) {
+                double wb = hist[b];
+                if (tail + wb >= target) {
+                    /* inside bin b: tail(d) = tail + wb * ((b+1) w - d) / w */
+                    double f = (target - tail) / wb;   /* fraction of the bin beyond d */
+                    d = (b + 1.0 - f) * bin_w;
+                    break;
+                }
+                tail += wb;
+            }
+            if (d == INFINITY) d = 0.0;
+        }
+        thr[k - 1] = d;
+    }
+    return 0;
+}
+
+/* Adaptive run: n_initial primaries without enhancement, then epochs of
+ * epoch primaries, the cloning depths re-estimated from the accumulated
+ * histogram before each epoch.  The primaries of an epoch run in parallel
+ * with the epoch's depths frozen (Sec. 3: a track never sees its depths
+ * change).  thr_hist (epochs x 16, may be NULL) receives the depths used by
+ * each enhanced epoch; returns the number of enhanced epochs. */
+int o_run_adaptive(const o_params* P0, int64_t n_ions, int64_t n_initial, int64_t epoch, uint64_t seed,
+                   int nthreads, double* hist, int64_t* counters, double* counters_w, double* thr_hist,
+                   int max_epochs)
+{
+    o_params P = *P0;
+    int nthr = P0->nthr;
+    int64_t done = 0;
+    int ep = 0;
+    if (n_initial > n_ions) n_initial = n_ions;
+    if (n_initial > 0) {
+        P.nthr = 0;
+        o_run(&P, n_initial, 0, seed, nthreads, hist, counters, counters_w, NULL, NULL);
+        done = n_initial;
+    }
+    while (done < n_ions) {
+        int64_t m = n_ions - done < epoch ? n_ions - done : epoch;
+        P.nthr = nthr;
+        if (done > 0) {
+            double t[16];
+            if (o_update_thresholds(hist, P.nbins, P.bin_w, nthr, t) == 0)
+                for (int k = 0; k < nthr; ++k) P.thr[k] = t[k];
+        }
+        if (thr_hist && ep < max_epochs)
+            for (int k = 0; k < 16; ++k) thr_hist[16 * ep + k] = k < nthr ? P.thr[k] : 0.0;
+        o_run(&P, m, done, seed, nthreads, hist, counters, counters_w, NULL, NULL);
+        done += m;
+        ++ep;
+    }
+    return ep;
+}
+
 /* Convenience exports for the tests. */
 double o_ion_pair_energy(const o_params* P, double Z2, double r, double* dU)
 {

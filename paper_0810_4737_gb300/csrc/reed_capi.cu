@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <math_constants.h>
+
 #include "reed.h"
 #include "reed_internal.h"
 
@@ -70,6 +72,12 @@ struct reed_ctx {
     // scratch for diagnostics
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // adaptive cloning depths: current set and per-epoch history
+    double* d_thr = nullptr;
+    double* d_thr_hist = nullptr;
+    int thr_hist_cap = 0, thr_epochs = 0;
+    unsigned long long* d_finished = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0.0;
     LaunchCfg last_cfg{};
@@ -337,6 +345,44 @@ bool valid_threads(int t) { return t == 32 || t == 64 || t == 128 || t == 256; }
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Cloning-depth update at an epoch boundary (one thread): d_k = S^-1(2^-k)
+// with S(d) the weighted fraction of finished tracks that stopped at depth
+// >= d, read off the range histogram (nbins + under, over, back) with linear
+// interpolation inside a bin; +inf when the target weight lies beyond the
+// histogram.  An empty histogram leaves the depths unchanged.  The new set
+// is also appended to the history row.
+// ---------------------------------------------------------------------------
+static __global__ void update_thresholds_kernel(const double* __restrict__ hist, int nbins, double bin_w, int nthr,
+                                         double* __restrict__ thr, double* __restrict__ history_row)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double total = 0.0;
+    for (int b = 0; b < nbins + 3; ++b) total += hist[b];
+    if (total > 0.0) {
+        const double beyond = hist[nbins + 1];
+        for (int k = 1; k <= nthr; ++k) {
+            const double target = ldexp(total, -k);
+            double d = CUDART_INF;
+            if (beyond < target) {
+                double tail = beyond;
+                d = 0.0;
+                for (int b = nbins - 1; b >= 0; --b) {
+                    const double wb = hist[b];
+                    if (tail + wb >= target) {
+                        d = ((double)b + 1.0 - (target - tail) / wb) * bin_w;
+                        break;
+                    }
+                    tail += wb;
+                }
+            }
+            thr[k - 1] = d;
+        }
+    }
+    if (history_row)
+        for (int k = 0; k < REED_MAX_THR; ++k) history_row[k] = k < nthr ? thr[k] : 0.0;
+}
+
 extern "C" {
 
 int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, int n_species,
@@ -384,6 +430,9 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
         cudaMalloc((void**)&ctx->d_next, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_status, sizeof(int)) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_rec_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_thr, sizeof(double) * REED_MAX_THR) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_finished, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
         reed_destroy(ctx);
         return fail(nullptr, REED_E_NOMEM, "device allocation failed");
@@ -490,10 +539,100 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     B.trace_anchor = ctx->d_trace_anchor;
     B.status = ctx->d_status;
 
-    CK(cudaMemsetAsync(ctx->d_next, 0, sizeof(unsigned long long), st));
+    B.thr = ctx->d_thr;
+    B.finished = ctx->d_finished;
+    P.stop_after = o.target_tracks;
+
+    // epochs: one launch, or (adaptive) unenhanced primaries followed by
+    // epochs whose cloning depths are re-estimated on the device first
+    struct Epoch {
+        int64_t first, count;
+        int nthr, update, guess;
+    };
+    std::vector<Epoch> ep;
+    if (!o.adaptive) {
+        ep.push_back({o.first_id, n_ions, P.nthr, 0, 0});
+    } else {
+        if (o.epoch_size < 1 || o.n_initial < 0 || P.nthr < 1)
+            return fail(ctx, REED_E_ARG, "adaptive runs need epoch_size >= 1, n_initial >= 0, n_thresholds >= 1");
+        const int64_t ninit = std::min<int64_t>(o.n_initial, n_ions);
+        int64_t done = 0;
+        if (ninit > 0) {
+            ep.push_back({o.first_id, ninit, 0, 0, 0});
+            done = ninit;
+        }
+        bool first_enh = true;
+        while (done < n_ions) {
+            const int64_t m = std::min<int64_t>(o.epoch_size, n_ions - done);
+            const int guess = (first_enh && ninit == 0) ? 1 : 0;
+            ep.push_back({o.first_id + done, m, P.nthr, guess ? 0 : 1, guess});
+            done += m;
+            first_enh = false;
+        }
+        int nenh = 0;
+        for (const Epoch& e : ep) nenh += e.nthr > 0;
+        if (nenh > ctx->thr_hist_cap) {
+            if ((rc = dev_alloc(ctx, &ctx->d_thr_hist, sizeof(double) * REED_MAX_THR * (size_t)nenh))) return rc;
+            ctx->thr_hist_cap = nenh;
+        }
+        ctx->thr_epochs = nenh;
+        CK(cudaMemcpy(ctx->d_thr, o.thresholds, sizeof(double) * REED_MAX_THR, cudaMemcpyHostToDevice));
+    }
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(ctx->d_finished, 0, sizeof(unsigned long long), st));
+
+    // the device work of the run, on stream s
+    auto enqueue = [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        int row = 0;
+        for (const Epoch& x : ep) {
+            if (x.count <= 0) continue;
+            DevParams Pe = P;
+            Pe.first_id = x.first;
+            Pe.n_primaries = x.count;
+            Pe.nthr = x.nthr;
+            Pe.thr_from_device = (o.adaptive && x.nthr > 0) ? 1 : 0;
+            if ((e = cudaMemsetAsync(ctx->d_next, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+            if (o.adaptive && x.nthr > 0) {
+                double* hrow = ctx->d_thr_hist + (size_t)REED_MAX_THR * row++;
+                if (x.update) {
+                    update_thresholds_kernel<<<1, 1, 0, s>>>(ctx->d_hist, ctx->nbins, ctx->bin_w, x.nthr, ctx->d_thr,
+                                                             hrow);
+                    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                } else if ((e = cudaMemcpyAsync(hrow, ctx->d_thr, sizeof(double) * REED_MAX_THR,
+                                                cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+                    return e;
+                }
+            }
+            e = f64 ? reed_f64::launch_track(tt, Pe, B, L, s) : reed_f32::launch_track(tt, Pe, B, L, s);
+            if (e != cudaSuccess) return e;
+        }
+        return e;
+    };
     CK(cudaEventRecord(ctx->ev0, st));
-    if (n_ions > 0) CK(f64 ? reed_f64::launch_track(tt, P, B, L, st) : reed_f32::launch_track(tt, P, B, L, st));
+    if (ep.size() > 1) {
+        // several dependent launches: capture them once into a CUDA graph
+        cudaEvent_t ready = ctx->ev1;
+        CK(cudaEventRecord(ready, st));
+        CK(cudaStreamWaitEvent(ctx->cap_stream, ready, 0));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = enqueue(ctx->cap_stream);
+        cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        CK(ce);
+        CK(ee);
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        cudaError_t le = cudaGraphLaunch(exec, st);
+        cudaError_t se = cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(exec);
+        CK(le);
+        CK(se);
+    } else {
+        CK(enqueue(st));
+    }
     CK(cudaEventRecord(ctx->ev1, st));
     CK(cudaStreamSynchronize(st));
     float ms = 0.f;
@@ -581,6 +720,16 @@ int reed_trace(reed_ctx* ctx, double* traj, int32_t* anchors, int n_tracks, int 
     return REED_OK;
 }
 
+int reed_thresholds(reed_ctx* ctx, double* history, int max_epochs, int* n_epochs)
+{
+    if (!ctx || !n_epochs || max_epochs < 0) return REED_E_ARG;
+    *n_epochs = ctx->thr_epochs;
+    const int m = std::min(max_epochs, ctx->thr_epochs);
+    if (m > 0 && history)
+        CK(cudaMemcpy(history, ctx->d_thr_hist, sizeof(double) * REED_MAX_THR * m, cudaMemcpyDefault));
+    return REED_OK;
+}
+
 int reed_reset(reed_ctx* ctx)
 {
     if (!ctx) return REED_E_ARG;
@@ -601,9 +750,11 @@ void reed_destroy(reed_ctx* ctx)
 {
     if (!ctx) return;
     void* ptrs[] = {ctx->d_hist, ctx->d_counters, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
-                    ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch};
+                    ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch,
+                    ctx->d_thr, ctx->d_thr_hist, ctx->d_finished};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -846,6 +997,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     if (o.ctas_per_sm < 0) return fail(nullptr, REED_E_ARG, "negative ctas_per_sm");
     if (o.record_tracks || o.trace_tracks || o.trace_steps)
         return fail(nullptr, REED_E_ARG, "reed_run_static keeps no per-track records or traces");
+    if (o.adaptive) return fail(nullptr, REED_E_ARG, "reed_run_static runs fixed cloning depths only");
 
     // device parameters from a host-only description of the target
     reed_ctx desc;
@@ -904,6 +1056,9 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     B.next = reinterpret_cast<unsigned long long*>(base + 512);
     B.status = reinterpret_cast<int*>(base + 768);
     B.record_count = reinterpret_cast<unsigned long long*>(base + 1024);
+    B.finished = reinterpret_cast<unsigned long long*>(base + 1280);
+    B.thr = nullptr;
+    P.stop_after = o.target_tracks;
     B.stacks = P.nthr > 0 ? base + REED_STATIC_HEADER : nullptr;
     B.hist = hist_out;
     B.records = nullptr;

@@ -90,6 +90,8 @@ struct DevParams {
     // rare-event enhancement (Sec. 2)
     int nthr;
     double thr[REED_MAX_THR];
+    int thr_from_device;               // read the depths from DevBuf::thr (adaptive epochs)
+    long long stop_after;              // stop handing out primaries after this many tracks (0: never)
     // tallies
     int nbins;
     double bin_w;
@@ -114,6 +116,8 @@ struct DevBuf {
     size_t stack_stride, entry_bytes;
     int stack_depth;
     int* status;                    // [0] OR of error bits
+    const double* thr;              // cloning depths of this launch (adaptive epochs)
+    unsigned long long* finished;   // tracks finished in this run (stop rule)
 };
 
 enum { ERR_QUEUE = 1, ERR_NONFINITE = 2, ERR_NEIGHBOR = 4 };

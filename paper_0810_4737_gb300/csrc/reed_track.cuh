@@ -53,6 +53,8 @@ template <typename R> struct TrackShared {
     R dt;
     R rel[3];             // ion position relative to the anchor corner A a
     R zthr, zback, zsurf; // next cloning depth, backscatter plane, surface in the anchor frame
+    double thr[REED_MAX_THR];  // this track's cloning depths (frozen while it runs)
+    int nthr;
     int Aold[3];
     int shift, rebuild, event, status, src, top, nclone;
     int need_count, active_count, n_out, out_ovf;
@@ -745,6 +747,7 @@ template <typename R> __device__ void finish_track(const DevParams& P, const Dev
     } else {
         atomicAdd(&B.wsum[W_FAILED], w);
     }
+    if (P.stop_after > 0) atomicAdd(B.finished, 1ull);
     if (P.record) {
         unsigned long long k = atomicAdd(B.record_count, 1ull);
         if ((long long)k < P.record_cap) {
@@ -804,7 +807,7 @@ template <typename R> __device__ void set_frame(const DevParams& P, TrackShared<
     const IonState<R>& I = S->ion;
     for (int d = 0; d < 3; ++d) S->rel[d] = R(I.x[d] - (double)I.A[d] * P.a);
     const double z0 = (double)I.A[2] * P.a;
-    S->zthr = I.level < P.nthr ? R(P.thr[I.level] - z0) : R(1e30);
+    S->zthr = I.level < S->nthr ? R(S->thr[I.level] - z0) : R(1e30);
     S->zback = R(-P.rc - z0);
     S->zsurf = R(-z0);
 }
@@ -887,7 +890,7 @@ __device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShar
     int nc = 0;
     if (S->rel[2] >= S->zthr) {
         // passed one (or more) cloning depths: count them on the FP64 depth
-        while (I.level + nc < P.nthr && I.x[2] >= P.thr[I.level + nc]) ++nc;
+        while (I.level + nc < S->nthr && I.x[2] >= S->thr[I.level + nc]) ++nc;
     }
     S->nclone = nc;
     return nc ? EV_CLONE : EV_NONE;
@@ -981,8 +984,13 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
         // ---- acquire a track: own clone stack first, then a new primary
         if (tid == 0) {
             S->rebuild = 0;
+            S->nthr = P.nthr;
+            for (int k = 0; k < P.nthr; ++k) S->thr[k] = P.thr_from_device ? B.thr[k] : P.thr[k];
             if (S->top > 0) {
                 S->src = SRC_CLONE;
+            } else if (P.stop_after > 0 &&
+                       (long long)(*(volatile unsigned long long*)B.finished) >= P.stop_after) {
+                S->src = SRC_NONE;   // enough tracks collected: hand out no more primaries
             } else {
                 unsigned long long k = atomicAdd(B.next, 1ull);
                 S->pidx = (long long)k;

@@ -49,7 +49,8 @@ class reed_run_opts(C.Structure):
                 ("bin_width", C.c_double), ("first_id", C.c_int64), ("threads_per_track", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("record_tracks", C.c_int32), ("trace_tracks", C.c_int32),
                 ("trace_steps", C.c_int32), ("reserved", C.c_int32), ("record_capacity", C.c_int64),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("adaptive", C.c_int32), ("reserved2", C.c_int32),
+                ("epoch_size", C.c_int64), ("n_initial", C.c_int64), ("target_tracks", C.c_int64)]
 
 
 class reed_track_record(C.Structure):
@@ -78,7 +79,7 @@ class reed_stats_t(C.Structure):
 
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",
             "reed_reset", "reed_last_error", "reed_destroy", "reed_philox", "reed_cell_atoms", "reed_forces",
-            "reed_window_replay", "reed_run_static"]
+            "reed_window_replay", "reed_run_static", "reed_thresholds"]
 
 _LIB = None
 _D = C.POINTER(C.c_double)
@@ -114,6 +115,7 @@ def lib():
         L.reed_track_records.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_int64)]
         L.reed_trace.argtypes = [vp, vp, vp, C.c_int, C.c_int]
         L.reed_reset.argtypes = [vp]
+        L.reed_thresholds.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int)]
         L.reed_last_error.argtypes = [vp]
         L.reed_last_error.restype = C.c_char_p
         L.reed_destroy.argtypes = [vp]
@@ -171,7 +173,8 @@ def potentials_struct(w) -> reed_potentials:
 
 
 def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, record=True, record_capacity=0,
-             trace_tracks=0, trace_steps=0, stream=None) -> reed_run_opts:
+             trace_tracks=0, trace_steps=0, stream=None, adaptive=False, epoch_size=4096, n_initial=50,
+             target_tracks=0) -> reed_run_opts:
     o = reed_run_opts()
     o.dt_max_fs, o.dx_max, o.e_stop = w["dt_max_fs"], w["dx_max"], w["e_stop"]
     o.step_cap = int(w["step_cap"])
@@ -188,6 +191,8 @@ def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, reco
     o.record_capacity = record_capacity
     o.trace_tracks, o.trace_steps = trace_tracks, trace_steps
     o.stream = stream
+    o.adaptive = 1 if adaptive else 0
+    o.epoch_size, o.n_initial, o.target_tracks = epoch_size, n_initial, target_tracks
     return o
 
 
@@ -232,6 +237,16 @@ def reed_trace(ctx, n_tracks, n_steps):
     anc = np.zeros((n_tracks, n_steps, 3), dtype=np.int32)
     _check(lib().reed_trace(ctx, traj.ctypes.data, anc.ctypes.data, n_tracks, n_steps), ctx)
     return traj, anc
+
+
+def reed_thresholds(ctx, max_epochs=1024):
+    """Cloning depths of each enhanced epoch of the last adaptive run."""
+    n = C.c_int(0)
+    _check(lib().reed_thresholds(ctx, None, 0, C.byref(n)), ctx)
+    h = np.zeros((min(n.value, max_epochs), 16))
+    if h.shape[0]:
+        _check(lib().reed_thresholds(ctx, h.ctypes.data, h.shape[0], C.byref(n)), ctx)
+    return h
 
 
 def reed_reset(ctx):
@@ -336,6 +351,9 @@ class Reed:
 
     def reset(self):
         reed_reset(self.ctx)
+
+    def thresholds(self):
+        return reed_thresholds(self.ctx)
 
     def forces(self, ion_x, xyz, sp, precision=PREC_MIXED):
         ion = self.w["ion"]

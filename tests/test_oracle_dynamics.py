@@ -152,3 +152,61 @@ def test_time_step_grows_as_the_ion_slows(O):
     assert np.mean(np.abs(dt[1:][hi] * vprev[hi] - 0.05) < 1e-9) > 0.9
     # anchors move by at most one cell per axis per step
     assert np.max(np.abs(np.diff(anc, axis=0))) <= 1
+
+
+def test_threshold_update_uniform_is_exact(O):
+    """Uniform stopping depths on [0, L): S(d) = 1 - d/L, so S^-1(2^-k) =
+    L (1 - 2^-k); linear interpolation inside bins is exact for it."""
+    nb, w = 400, 2.0
+    L = nb * w
+    hist = np.zeros(nb + 3)
+    hist[:nb] = 3.0
+    thr = O.update_thresholds(hist, w, 12)
+    k = np.arange(1, 13)
+    np.testing.assert_allclose(thr, L * (1 - 2.0 ** -k), rtol=1e-13)
+    # backscattered / above-surface weight counts as not reaching any depth
+    hist2 = hist.copy()
+    hist2[nb] = 100.0        # above the surface
+    hist2[nb + 2] = 200.0    # backscattered
+    tot = hist2.sum()
+    thr2 = O.update_thresholds(hist2, w, 3)
+    for kk, d in enumerate(thr2, start=1):
+        np.testing.assert_allclose(3.0 * (L - d) / w, tot * 2.0 ** -kk, rtol=1e-12)
+
+
+def test_threshold_update_exponential_closed_form(O):
+    """Exponential depths with decay length lam: S^-1(2^-k) = k lam ln 2;
+    histogram bins of lam/200 give the inversion to bin-interpolation accuracy."""
+    lam, nb = 100.0, 4000
+    w = lam / 200.0
+    edges = np.arange(nb + 1) * w
+    hist = np.zeros(nb + 3)
+    hist[:nb] = np.exp(-edges[:-1] / lam) - np.exp(-edges[1:] / lam)
+    hist[nb + 1] = np.exp(-edges[-1] / lam)   # beyond the last bin
+    thr = O.update_thresholds(hist, w, 12)
+    np.testing.assert_allclose(thr, np.arange(1, 13) * lam * np.log(2.0), rtol=2e-5)
+    # a target deeper than the histogram gives no depth (+inf)
+    hist3 = np.zeros(nb + 3)
+    hist3[0] = 0.7
+    hist3[nb + 1] = 0.3
+    t3 = O.update_thresholds(hist3, w, 2)
+    np.testing.assert_allclose(t3[0], (1.0 - 0.2 / 0.7) * w, rtol=1e-13)   # 0.5 = 0.3 + 0.7 f
+    assert np.isinf(t3[1])                                                 # 0.25 < 0.3 beyond
+
+
+def test_adaptive_run_converges_and_conserves(O):
+    w = workload("b1kev_si_0k_zbl", sigma=0.076, rot=(0.0, 45.0), energy=2000.0,
+                 thresholds=[30.0, 60.0, 90.0, 120.0, 150.0, 180.0], n_bins=200, bin_w=2.0)
+    p = O.params(w)
+    r = O.run_adaptive(p, 800, 50, 250, seed=1, threads=8)
+    assert r["epochs"] == 3
+    th = r["thresholds"]
+    # the first enhanced epoch uses the depths estimated from the 50
+    # unenhanced ions; every set ascends; the estimates settle
+    fin = np.isfinite(th[0])
+    assert np.all(np.diff(th[0][fin]) > 0)
+    both = np.isfinite(th[-1]) & np.isfinite(th[-2])
+    assert both.sum() >= 4
+    assert np.max(np.abs(th[-1][both] - th[-2][both]) / th[-1][both]) < 0.5
+    total = r["hist"].sum() + r["under"] + r["over"] + r["back"] + r["w_trunc"]
+    assert total == 800.0

@@ -149,6 +149,15 @@ typedef struct {
      * finished; tracks already running are completed (the paper's kill
      * signal, Sec. 3).  0 = run all n_ions. */
     int64_t target_tracks;
+    /* Cumulative damage (the paper's shared damage information, Sec. 1, 3):
+     * an atom leaving the simulation -- its cell dropped behind the ion, or the
+     * track finished -- deposits weight x kinetic energy, when above
+     * damage_min, into a damage_n^3 grid of damage_voxel cubes with origin
+     * (-damage_n damage_voxel / 2, same, 0).  damage_n = 0: no map. */
+    int32_t damage_n;
+    int32_t reserved3;
+    double damage_voxel;       /* A */
+    double damage_min;         /* eV */
 } reed_run_opts;
 
 /* Per-track result: the depth and weight of one finished track (Sec. 3, result messages). */
@@ -217,6 +226,11 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
  * n_bins must equal the tally's bin count.  Errors: REED_E_STATE (no run),
  * REED_E_ARG. */
 int reed_range_profile(reed_ctx* ctx, double* bins_out, int n_bins, double* extra3);
+
+/* Cumulative damage map of all runs since init/reset: out (host or device)
+ * receives n^3 doubles (eV, index (ix n + iy) n + iz), overflow (may be
+ * NULL) the energy deposited outside the grid.  n must equal damage_n. */
+int reed_damage_map(reed_ctx* ctx, double* out, int n, double* overflow);
 
 /* Counters of all runs since init/reset (host pointer). */
 int reed_stats(reed_ctx* ctx, reed_stats_t* out);

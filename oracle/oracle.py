@@ -58,6 +58,7 @@ class Params(C.Structure):
         ("beam_mode", C.c_int),
         ("nthr", C.c_int), ("thr", C.c_double * 16),
         ("nbins", C.c_int), ("bin_w", C.c_double),
+        ("dn", C.c_int), ("dvox", C.c_double), ("dmin", C.c_double),
     ]
 
 
@@ -104,6 +105,10 @@ def lib():
             L.o_run.argtypes = [_P, C.c_int64, C.c_int64, C.c_uint64, C.c_int, _D,
                                 C.POINTER(C.c_int64), _D, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]
             L.o_free.argtypes = [C.c_void_p]
+            L.o_run_damage.argtypes = [_P, C.c_int64, C.c_int64, C.c_uint64, C.c_int, _D,
+                                       C.POINTER(C.c_int64), _D, C.POINTER(C.c_void_p), C.POINTER(C.c_int64), _D]
+            L.o_track_energy.argtypes = [_P, C.c_uint64, C.c_uint64, _D]
+            L.o_track_energy.restype = C.c_int
             L.o_trace.argtypes = [_P, C.c_uint64, C.c_uint64, C.c_int, _D, _I]
             L.o_trace.restype = C.c_int
             L.o_window_replay.argtypes = [_P, C.c_uint64, C.c_int, _D, _I, C.c_int, _I, _I, _D]
@@ -175,6 +180,7 @@ def params(w: dict, screening: int = 1) -> Params:
     for i, d in enumerate(thr):
         p.thr[i] = d
     p.nbins, p.bin_w = int(w["n_bins"]), float(w["bin_w"])
+    p.dn, p.dvox, p.dmin = int(w.get("damage_n", 0)), float(w.get("damage_voxel", 10.0)), float(w.get("damage_min", 0.1))
     return p
 
 
@@ -269,12 +275,16 @@ def run(p: Params, n_ions: int, seed: int, first_id: int = 0, threads: int | Non
         threads = os.cpu_count() or 1
     ptr = C.c_void_p()
     nrec = C.c_int64(0)
-    lib().o_run(C.byref(p), n_ions, first_id, seed, threads, _dp(hist),
-                cnt.ctypes.data_as(C.POINTER(C.c_int64)), _dp(wt),
-                C.byref(ptr) if records else None, C.byref(nrec))
+    dmg = np.zeros(p.dn ** 3 + 1) if p.dn > 0 else None
+    lib().o_run_damage(C.byref(p), n_ions, first_id, seed, threads, _dp(hist),
+                       cnt.ctypes.data_as(C.POINTER(C.c_int64)), _dp(wt),
+                       C.byref(ptr) if records else None, C.byref(nrec), _dp(dmg) if dmg is not None else None)
     out = {"hist": hist[:p.nbins].copy(), "under": hist[p.nbins], "over": hist[p.nbins + 1],
            "back": hist[p.nbins + 2], "w_trunc": wt[0], "steps": int(cnt[0]),
            "tracks": int(cnt[1]), "clones": int(cnt[2]), "shifts": int(cnt[3])}
+    if dmg is not None:
+        out["damage"] = dmg[:-1].reshape(p.dn, p.dn, p.dn)
+        out["damage_overflow"] = dmg[-1]
     if records:
         n = nrec.value
         buf = (C.c_char * (n * RECORD_DTYPE.itemsize)).from_address(ptr.value)
@@ -344,3 +354,12 @@ def run_adaptive(p: Params, n_ions: int, n_initial: int, epoch: int, seed: int, 
     return {"hist": hist[:p.nbins].copy(), "under": hist[p.nbins], "over": hist[p.nbins + 1],
             "back": hist[p.nbins + 2], "w_trunc": wt[0], "steps": int(cnt[0]), "tracks": int(cnt[1]),
             "clones": int(cnt[2]), "thresholds": th[:min(ne, max_epochs), :p.nthr].copy(), "epochs": ne}
+
+
+def track_energy(p: Params, seed: int, track_id: int) -> dict:
+    """Energy bookkeeping of one primary (no cloning); needs p.dn > 0."""
+    out = np.zeros(8)
+    if lib().o_track_energy(C.byref(p), seed, track_id, _dp(out)) != 0:
+        raise ValueError("needs a damage grid and <= 1024 bins")
+    keys = ["E0", "ke_ion", "pe", "e_elec", "deposited", "below_threshold", "ke_window", "steps"]
+    return dict(zip(keys, out.tolist()))

@@ -86,6 +86,10 @@ typedef struct {
     double thr[16];
     int nbins;
     double bin_w;
+    /* cumulative damage map (reading): dn^3 voxels of dvox A, origin
+     * (-dn dvox / 2, -dn dvox / 2, 0); atoms with KE > dmin deposit w KE */
+    int dn;
+    double dvox, dmin;
 } o_params;
 
 typedef struct {
@@ -335,6 +339,35 @@ double o_rho0(const o_params* P)
     return N * 8.0 * O_PI * P->lam_loc * P->lam_loc * P->lam_loc;
 }
 
+/* Tallies of finished tracks (per worker thread). */
+typedef struct {
+    double* hist;      /* nbins + 3: under, over, back -- appended */
+    double* damage;    /* dn^3 + 1 (overflow) or NULL */
+    double w_trunc;
+    double e_dep_sub;  /* weighted KE of dropped atoms below the damage threshold */
+    int64_t steps, tracks, clones, shifts;
+} o_tally;
+
+/* Deposit the kinetic energy of window atom j (weight w) into the damage map. */
+static void o_deposit(const o_params* P, o_tally* T, const double* x, const double* v, double m, double w)
+{
+    if (!T || !T->damage || P->dn <= 0) return;
+    double ke = 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(ke > P->dmin)) {
+        T->e_dep_sub += w * ke;
+        return;
+    }
+    double half = 0.5 * P->dn * P->dvox;
+    int ix = (int)floor((x[0] + half) / P->dvox);
+    int iy = (int)floor((x[1] + half) / P->dvox);
+    int iz = (int)floor(x[2] / P->dvox);
+    size_t n = (size_t)P->dn;
+    if (ix < 0 || iy < 0 || iz < 0 || ix >= P->dn || iy >= P->dn || iz >= P->dn)
+        T->damage[n * n * n] += w * ke;
+    else
+        T->damage[((size_t)ix * n + iy) * n + iz] += w * ke;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Window / ion state                                                       */
 /* ------------------------------------------------------------------------ */
@@ -442,7 +475,7 @@ static void o_add_cell(const o_params* P, o_win* W, uint64_t key, const int c[3]
 
 /* Re-anchor the window on the ion: drop atoms whose home cell left the
  * window, create the cells that entered it.  Returns the number of moves. */
-static int o_window_update(const o_params* P, o_win* W, const o_ion* I, uint64_t key)
+static int o_window_update(const o_params* P, o_win* W, const o_ion* I, uint64_t key, o_tally* T)
 {
     int A[3];
     for (int d = 0; d < 3; ++d) A[d] = o_anchor1(P, I->x[d]);
@@ -452,7 +485,10 @@ static int o_window_update(const o_params* P, o_win* W, const o_ion* I, uint64_t
         /* drop */
         int k = 0;
         for (int j = 0; j < W->n; ++j) {
-            if (!o_in_window(P, A, &W->cell[3 * j])) continue;
+            if (!o_in_window(P, A, &W->cell[3 * j])) {
+                o_deposit(P, T, &W->x[3 * j], &W->v[3 * j], P->M2[W->sp[j]], ldexp(1.0, -I->level));
+                continue;
+            }
             if (k != j) {
                 for (int d = 0; d < 3; ++d) {
                     W->x[3 * k + d] = W->x[3 * j + d];
@@ -699,7 +735,7 @@ static double o_mass(const o_params* P, int s) { return P->M2[s]; }
 
 /* One step.  key: Philox key for newly created cells (<0 lattice: none). */
 static double o_step(const o_params* P, const o_consts* K, o_ion* I, o_win* W, uint64_t key,
-                     double dt_fixed, int windowing, int* moved)
+                     double dt_fixed, int windowing, int* moved, o_tally* T)
 {
     double dt = dt_fixed > 0.0 ? dt_fixed : o_pick_dt(P, I, W);
     double Fe[3];
@@ -721,7 +757,7 @@ static double o_step(const o_params* P, const o_consts* K, o_ion* I, o_win* W, u
         for (int d = 0; d < 3; ++d) W->x[3 * j + d] += dt * W->v[3 * j + d];
     }
     /* window */
-    *moved = (windowing && P->lattice >= 0) ? o_window_update(P, W, I, key) : 0;
+    *moved = (windowing && P->lattice >= 0) ? o_window_update(P, W, I, key, T) : 0;
     /* forces at the new positions */
     double U = o_forces(P, I->x, 1, W->n, W->x, W->sp, I->f, W->f, &I->rho);
     /* second half kick */
@@ -788,12 +824,6 @@ static int o_window_capacity(const o_params* P)
 /* ------------------------------------------------------------------------ */
 /* Tallies                                                                  */
 /* ------------------------------------------------------------------------ */
-typedef struct {
-    double* hist;      /* nbins + 3: under, over, back -- appended */
-    double w_trunc;
-    int64_t steps, tracks, clones, shifts;
-} o_tally;
-
 static void o_tally_finish(const o_params* P, o_tally* T, const o_ion* I, int status)
 {
     double w = ldexp(1.0, -I->level);
@@ -862,7 +892,7 @@ static int o_run_lineage(const o_params* P, const o_consts* K, uint64_t seed, ui
         int st = O_ALIVE;
         while (st == O_ALIVE) {
             int moved;
-            o_step(P, K, &I, &W, I.key, 0.0, 1, &moved);
+            o_step(P, K, &I, &W, I.key, 0.0, 1, &moved, T);
             T->shifts += moved;
             T->steps += 1;
             st = o_check(P, &I);
@@ -879,6 +909,8 @@ static int o_run_lineage(const o_params* P, const o_consts* K, uint64_t seed, ui
             }
         }
         o_tally_finish(P, T, &I, st);
+        for (int j = 0; j < W.n; ++j)
+            if (W.act[j]) o_deposit(P, T, &W.x[3 * j], &W.v[3 * j], P->M2[W.sp[j]], ldexp(1.0, -I.level));
         if (recs) {
             o_record R;
             R.id = I.id; R.primary = I.primary; R.z = I.x[2]; R.t = I.t;
@@ -908,17 +940,32 @@ static void o_consts_init(const o_params* P, o_consts* K)
  * counters_w[0].  If recs_out is not NULL it receives a malloc'ed array of
  * per-track records (ordered by primary, then depth-first), *nrec its length;
  * release it with o_free. */
+int o_run_damage(const o_params* P, int64_t n_ions, int64_t first_id, uint64_t seed, int nthreads,
+                 double* hist, int64_t* counters, double* counters_w, o_record** recs_out, int64_t* nrec,
+                 double* damage);
+
 int o_run(const o_params* P, int64_t n_ions, int64_t first_id, uint64_t seed, int nthreads,
           double* hist, int64_t* counters, double* counters_w, o_record** recs_out, int64_t* nrec)
+{
+    return o_run_damage(P, n_ions, first_id, seed, nthreads, hist, counters, counters_w, recs_out, nrec, NULL);
+}
+
+/* o_run plus the cumulative damage map (dn^3 voxels + overflow, accumulated
+ * into damage when not NULL). */
+int o_run_damage(const o_params* P, int64_t n_ions, int64_t first_id, uint64_t seed, int nthreads,
+                 double* hist, int64_t* counters, double* counters_w, o_record** recs_out, int64_t* nrec,
+                 double* damage)
 {
     o_consts K;
     o_consts_init(P, &K);
     int nb = P->nbins + 3;
+    size_t nd = (damage && P->dn > 0) ? (size_t)P->dn * P->dn * P->dn + 1 : 0;
     o_recbuf* bufs = recs_out ? (o_recbuf*)calloc((size_t)n_ions, sizeof(o_recbuf)) : NULL;
     int nt = nthreads > 0 ? nthreads : 1;
     double* hs = (double*)calloc((size_t)nt * nb, sizeof(double));
     int64_t* cs = (int64_t*)calloc((size_t)nt * 4, sizeof(int64_t));
     double* ws = (double*)calloc((size_t)nt, sizeof(double));
+    double* ds = nd ? (double*)calloc((size_t)nt * nd, sizeof(double)) : NULL;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
@@ -930,6 +977,7 @@ int o_run(const o_params* P, int64_t n_ions, int64_t first_id, uint64_t seed, in
         o_tally T;
         memset(&T, 0, sizeof(T));
         T.hist = &hs[(size_t)tid * nb];
+        T.damage = ds ? &ds[(size_t)tid * nd] : NULL;
         o_run_lineage(P, &K, seed, (uint64_t)(first_id + i), &T, bufs ? &bufs[i] : NULL);
         cs[tid * 4 + 0] += T.steps;
         cs[tid * 4 + 1] += T.tracks;
@@ -938,6 +986,7 @@ int o_run(const o_params* P, int64_t n_ions, int64_t first_id, uint64_t seed, in
         ws[tid] += T.w_trunc;
     }
     for (int t = 0; t < nt; ++t) {
+        for (size_t b = 0; b < nd; ++b) damage[b] += ds[(size_t)t * nd + b];
         for (int b = 0; b < nb; ++b) hist[b] += hs[(size_t)t * nb + b];
         for (int c = 0; c < 4; ++c) counters[c] += cs[t * 4 + c];
         counters_w[0] += ws[t];
@@ -958,6 +1007,60 @@ int o_run(const o_params* P, int64_t n_ions, int64_t first_id, uint64_t seed, in
     free(hs);
     free(cs);
     free(ws);
+    free(ds);
+    return 0;
+}
+
+/* Energy bookkeeping of one primary followed without cloning (for the
+ * damage-map balance): out = {E0, final ion KE, final potential energy of
+ * the window, energy to electronic stopping, deposited (map + overflow),
+ * kinetic energy below the deposit threshold, final window kinetic energy
+ * (integrated atoms), steps}. */
+int o_track_energy(const o_params* P0, uint64_t seed, uint64_t id, double* out)
+{
+    o_params P = *P0;
+    P.nthr = 0;
+    o_consts K;
+    o_consts_init(&P, &K);
+    size_t nd = (size_t)P.dn * P.dn * P.dn + 1;
+    o_tally T;
+    memset(&T, 0, sizeof(T));
+    double hist_local[1024 + 3];
+    if (P.nbins + 3 > 1027 || P.dn <= 0) return -1;
+    memset(hist_local, 0, sizeof(hist_local));
+    T.hist = hist_local;
+    T.damage = (double*)calloc(nd, sizeof(double));
+    o_ion I;
+    o_win W;
+    o_win_alloc(&W, o_window_capacity(&P));
+    o_launch(&P, seed, id, &I);
+    o_window_init(&P, &W, &I, I.key);
+    double U = o_forces(&P, I.x, 1, W.n, W.x, W.sp, I.f, W.f, &I.rho);
+    double E0 = 0.5 * P.M1 * (I.v[0] * I.v[0] + I.v[1] * I.v[1] + I.v[2] * I.v[2]) + U;
+    int st = O_ALIVE;
+    while (st == O_ALIVE) {
+        int moved;
+        U = o_step(&P, &K, &I, &W, I.key, 0.0, 1, &moved, &T);
+        st = o_check(&P, &I);
+    }
+    double ke_win = 0.0;
+    for (int j = 0; j < W.n; ++j) {
+        if (!W.act[j]) continue;
+        ke_win += 0.5 * P.M2[W.sp[j]] *
+                  (W.v[3 * j] * W.v[3 * j] + W.v[3 * j + 1] * W.v[3 * j + 1] + W.v[3 * j + 2] * W.v[3 * j + 2]);
+    }
+    double dep = 0.0;
+    for (size_t b = 0; b < nd; ++b) dep += T.damage[b];
+    out[0] = E0;
+    out[1] = 0.5 * P.M1 * (I.v[0] * I.v[0] + I.v[1] * I.v[1] + I.v[2] * I.v[2]);
+    out[2] = U;
+    out[3] = I.e_elec;
+    out[4] = dep;
+    out[5] = T.e_dep_sub;
+    out[6] = ke_win;
+    out[7] = (double)I.steps;
+    free(T.damage);
+    o_win_free(&W);
     return 0;
 }
 
@@ -978,7 +1081,7 @@ int o_trace(const o_params* P, uint64_t seed, uint64_t id, int nsteps, double* o
     for (s = 0; s < nsteps; ++s) {
         double t0 = I.t;
         int moved;
-        o_step(P, &K, &I, &W, I.key, 0.0, 1, &moved);
+        o_step(P, &K, &I, &W, I.key, 0.0, 1, &moved, NULL);
         double* o = &out[8 * s];
         o[0] = I.x[0]; o[1] = I.x[1]; o[2] = I.x[2]; o[3] = I.t;
         o[4] = I.v[0]; o[5] = I.v[1]; o[6] = I.v[2]; o[7] = I.t - t0;
@@ -1004,7 +1107,7 @@ int o_window_replay(const o_params* P, uint64_t key, int npts, const double* pat
     o_window_init(P, &W, &I, key);
     for (int p = 0; p < npts; ++p) {
         memcpy(I.x, &path[3 * p], 3 * sizeof(double));
-        o_window_update(P, &W, &I, key);
+        o_window_update(P, &W, &I, key, NULL);
         anchors[3 * p] = W.A[0]; anchors[3 * p + 1] = W.A[1]; anchors[3 * p + 2] = W.A[2];
     }
     int n = W.n;
@@ -1052,7 +1155,7 @@ int o_md_explicit(const o_params* P, double* ion_x, double* ion_v, int n, double
         }
         if (s == nsteps) break;
         int moved;
-        U = o_step(P, &K, &I, &W, 0, dt_fixed, 0, &moved);
+        U = o_step(P, &K, &I, &W, 0, dt_fixed, 0, &moved, NULL);
         if (0.5 * P->M1 * (I.v[0] * I.v[0] + I.v[1] * I.v[1] + I.v[2] * I.v[2]) < P->e_stop) { ++s; break; }
         if (stop_sep > 0.0 && n > 0) {
             double rv[3], r = o_dist(I.x, &W.x[0], rv);

@@ -72,6 +72,10 @@ struct reed_ctx {
     // scratch for diagnostics
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // cumulative damage map (fixed by the first run that asks for it)
+    double* d_damage = nullptr;
+    int dn = 0;
+    double dvox = 0.0;
     // adaptive cloning depths: current set and per-epoch history
     double* d_thr = nullptr;
     double* d_thr_hist = nullptr;
@@ -202,8 +206,12 @@ double lindhard_gamma(const reed_ctx* ctx, double Z1, double M1)
 // head-room for disorder and cascades (capped at the window size).
 int bond_capacity(const DevParams& P)
 {
-    if (P.tt != REED_TT_TERSOFF) return 0;
+    if (P.tt == REED_TT_NONE) return 0;
     if (P.margin == 0) return P.na;
+    if (P.tt == REED_TT_BUCKINGHAM) {   // lists of the integrated atoms only
+        const int k = P.n - 2 * P.margin;
+        return k * k * k * P.nb;
+    }
     const double rl = P.hd.tcut + kSkin;
     std::vector<double> x;
     std::vector<char> act;
@@ -298,6 +306,10 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.nbins = ctx->nbins;
     P.bin_w = ctx->bin_w;
     P.first_id = o.first_id;
+    P.dn = o.damage_n;
+    P.dvox = o.damage_voxel > 0 ? o.damage_voxel : 10.0;
+    P.dhalf = 0.5 * P.dn * P.dvox;
+    P.dmin = o.damage_min;
     fill_hot<float>(P.hf, P, ctx, kSkin);
     fill_hot<double>(P.hd, P, ctx, kSkin);
     P.bond_cap = bond_capacity(P);
@@ -403,8 +415,11 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
         if (!(sp[s].Z > 0) || !(sp[s].M > 0)) return fail(nullptr, REED_E_ARG, "species %d: Z and M must be > 0", s);
     if (!(pot->rc > 0) || !(pot->r_taper >= 0) || !(pot->r_taper < pot->rc))
         return fail(nullptr, REED_E_ARG, "need 0 <= r_taper < rc");
-    if (pot->target_model != REED_TT_NONE && pot->target_model != REED_TT_TERSOFF)
-        return fail(nullptr, REED_E_ARG, "target model %d is not available", pot->target_model);
+    if (pot->target_model != REED_TT_NONE && pot->target_model != REED_TT_TERSOFF &&
+        pot->target_model != REED_TT_BUCKINGHAM)
+        return fail(nullptr, REED_E_ARG, "unknown target model %d", pot->target_model);
+    if (pot->target_model == REED_TT_BUCKINGHAM && !(pot->buck_cut[1] > pot->buck_cut[0] && pot->buck_cut[0] >= 0))
+        return fail(nullptr, REED_E_ARG, "Buckingham needs 0 <= taper start < cutoff");
     if (pot->target_model == REED_TT_TERSOFF && lat->kind != REED_LATTICE_DIAMOND)
         return fail(nullptr, REED_E_ARG, "Tersoff needs the one-species diamond lattice");
     if (!(pot->lam_loc > 0)) return fail(nullptr, REED_E_ARG, "lam_loc must be > 0");
@@ -488,6 +503,19 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
         }
         P.record_cap = ctx->rec_cap;
     }
+    // damage map (kept across runs until reset; geometry fixed by the first run)
+    if (o.damage_n < 0 || o.damage_n > 512) return fail(ctx, REED_E_ARG, "damage_n must be 0..512");
+    if (o.damage_n > 0) {
+        if (!ctx->d_damage) {
+            const size_t nd = (size_t)o.damage_n * o.damage_n * o.damage_n + 1;
+            if ((rc = dev_alloc(ctx, &ctx->d_damage, sizeof(double) * nd))) return rc;
+            CK(cudaMemset(ctx->d_damage, 0, sizeof(double) * nd));
+            ctx->dn = o.damage_n;
+            ctx->dvox = P.dvox;
+        } else if (ctx->dn != o.damage_n || ctx->dvox != P.dvox) {
+            return fail(ctx, REED_E_ARG, "damage map is %d^3 x %g A since the last reset", ctx->dn, ctx->dvox);
+        }
+    }
     // trace buffers (per run)
     ctx->trace_tracks = o.trace_tracks;
     ctx->trace_steps = o.trace_steps;
@@ -541,6 +569,7 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
 
     B.thr = ctx->d_thr;
     B.finished = ctx->d_finished;
+    B.damage = o.damage_n > 0 ? ctx->d_damage : nullptr;
     P.stop_after = o.target_tracks;
 
     // epochs: one launch, or (adaptive) unenhanced primaries followed by
@@ -720,6 +749,17 @@ int reed_trace(reed_ctx* ctx, double* traj, int32_t* anchors, int n_tracks, int 
     return REED_OK;
 }
 
+int reed_damage_map(reed_ctx* ctx, double* out, int n, double* overflow)
+{
+    if (!ctx || !out) return REED_E_ARG;
+    if (!ctx->d_damage) return fail(ctx, REED_E_STATE, "no damage map since init/reset");
+    if (n != ctx->dn) return fail(ctx, REED_E_ARG, "damage map has %d voxels per edge", ctx->dn);
+    const size_t v = (size_t)n * n * n;
+    CK(cudaMemcpy(out, ctx->d_damage, sizeof(double) * v, cudaMemcpyDefault));
+    if (overflow) CK(cudaMemcpy(overflow, ctx->d_damage + v, sizeof(double), cudaMemcpyDefault));
+    return REED_OK;
+}
+
 int reed_thresholds(reed_ctx* ctx, double* history, int max_epochs, int* n_epochs)
 {
     if (!ctx || !n_epochs || max_epochs < 0) return REED_E_ARG;
@@ -738,6 +778,9 @@ int reed_reset(reed_ctx* ctx)
     if (ctx->d_records) cudaFree(ctx->d_records);
     ctx->d_records = nullptr;
     ctx->rec_cap = 0;
+    if (ctx->d_damage) cudaFree(ctx->d_damage);
+    ctx->d_damage = nullptr;
+    ctx->dn = 0;
     CK(cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT));
     CK(cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4));
     CK(cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long)));
@@ -751,7 +794,7 @@ void reed_destroy(reed_ctx* ctx)
     if (!ctx) return;
     void* ptrs[] = {ctx->d_hist, ctx->d_counters, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
                     ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch,
-                    ctx->d_thr, ctx->d_thr_hist, ctx->d_finished};
+                    ctx->d_thr, ctx->d_thr_hist, ctx->d_finished, ctx->d_damage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -978,8 +1021,11 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
         if (!(sp[s].Z > 0) || !(sp[s].M > 0)) return fail(nullptr, REED_E_ARG, "species %d: Z and M must be > 0", s);
     if (!(pot->rc > 0) || !(pot->r_taper >= 0) || !(pot->r_taper < pot->rc) || !(pot->lam_loc > 0))
         return fail(nullptr, REED_E_ARG, "invalid ion-target cutoff or density length");
-    if (pot->target_model != REED_TT_NONE && pot->target_model != REED_TT_TERSOFF)
-        return fail(nullptr, REED_E_ARG, "target model %d is not available", pot->target_model);
+    if (pot->target_model != REED_TT_NONE && pot->target_model != REED_TT_TERSOFF &&
+        pot->target_model != REED_TT_BUCKINGHAM)
+        return fail(nullptr, REED_E_ARG, "unknown target model %d", pot->target_model);
+    if (pot->target_model == REED_TT_BUCKINGHAM && !(pot->buck_cut[1] > pot->buck_cut[0] && pot->buck_cut[0] >= 0))
+        return fail(nullptr, REED_E_ARG, "Buckingham needs 0 <= taper start < cutoff");
     if (pot->target_model == REED_TT_TERSOFF && lat->kind != REED_LATTICE_DIAMOND)
         return fail(nullptr, REED_E_ARG, "Tersoff needs the one-species diamond lattice");
     if (!(ion_Z > 0) || !(ion_M > 0) || !(energy_eV > 0) || n_ions < 0)
@@ -998,6 +1044,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     if (o.record_tracks || o.trace_tracks || o.trace_steps)
         return fail(nullptr, REED_E_ARG, "reed_run_static keeps no per-track records or traces");
     if (o.adaptive) return fail(nullptr, REED_E_ARG, "reed_run_static runs fixed cloning depths only");
+    if (o.damage_n) return fail(nullptr, REED_E_ARG, "reed_run_static keeps no damage map");
 
     // device parameters from a host-only description of the target
     reed_ctx desc;
@@ -1058,6 +1105,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     B.record_count = reinterpret_cast<unsigned long long*>(base + 1024);
     B.finished = reinterpret_cast<unsigned long long*>(base + 1280);
     B.thr = nullptr;
+    B.damage = nullptr;
     P.stop_after = o.target_tracks;
     B.stacks = P.nthr > 0 ? base + REED_STATIC_HEADER : nullptr;
     B.hist = hist_out;

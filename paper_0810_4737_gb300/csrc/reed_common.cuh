@@ -18,7 +18,11 @@
 #define REED_MAX_BASIS 12
 #define REED_MAX_THR 16
 #define REED_MAX_WARPS 8
-#define REED_MAXNB 12           // target neighbours kept per atom
+#define REED_MAXNB 12           // Tersoff neighbours kept per atom
+#define REED_MAXNB_PAIR 64      // pair-potential neighbours kept per atom
+
+// neighbour-list capacity per atom for a target model
+__host__ __device__ constexpr int maxnb(int tt) { return tt == REED_TT_BUCKINGHAM ? REED_MAXNB_PAIR : REED_MAXNB; }
 
 // slot flags carried in pos.w (exact small integers in either precision):
 //   w = species (0/1) for an integrated atom, species + 2 for a frozen atom,
@@ -91,6 +95,9 @@ struct DevParams {
     int nthr;
     double thr[REED_MAX_THR];
     int thr_from_device;               // read the depths from DevBuf::thr (adaptive epochs)
+    // cumulative damage map: dn^3 voxels of dvox, origin (-dhalf, -dhalf, 0)
+    int dn;
+    double dvox, dhalf, dmin;
     long long stop_after;              // stop handing out primaries after this many tracks (0: never)
     // tallies
     int nbins;
@@ -117,6 +124,7 @@ struct DevBuf {
     int stack_depth;
     int* status;                    // [0] OR of error bits
     const double* thr;              // cloning depths of this launch (adaptive epochs)
+    double* damage;                 // dn^3 + 1 (overflow) voxels, or null
     unsigned long long* finished;   // tracks finished in this run (stop rule)
 };
 

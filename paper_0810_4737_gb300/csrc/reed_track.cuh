@@ -82,7 +82,7 @@ template <typename R, int TT> struct Layout {
                align(na) +                               // flags
                align(sizeof(uint16_t) * cap) +           // slot_atom
                align(cap) +                              // nnb
-               align(sizeof(uint16_t) * cap * REED_MAXNB) +  // nbr
+               align(sizeof(uint16_t) * cap * maxnb(TT)) +    // nbr
                align(sizeof(uint16_t) * REED_OUTCAP);    // outliers
     }
     static __host__ __device__ size_t bond_bytes(int cap)
@@ -139,7 +139,7 @@ template <typename R, int TT> struct Win {
             nnb = base + o;
             o += L::align(cap);
             nbr = reinterpret_cast<uint16_t*>(base + o);
-            o += L::align(sizeof(uint16_t) * cap * REED_MAXNB);
+            o += L::align(sizeof(uint16_t) * cap * maxnb(TT));
             outl = reinterpret_cast<uint16_t*>(base + o);
             o += L::align(sizeof(uint16_t) * REED_OUTCAP);
         }
@@ -232,6 +232,28 @@ __device__ __forceinline__ bool reanchor_atom(const DevParams& P, const HotParam
 }
 
 template <typename R> __device__ __forceinline__ bool is_present(const V4<R>& p) { return p.w >= R(0); }
+template <typename R> __device__ __forceinline__ int species_of(const V4<R>& p);
+
+// Cumulative damage (reading of the paper's shared damage information): an
+// atom leaving the simulation -- its cell dropped, or the track ended --
+// deposits w * KE into the voxel holding it when KE > dmin.  p is relative to
+// the anchor A.
+template <typename R>
+__device__ __forceinline__ void deposit_damage(const DevParams& P, const DevBuf& B, const V4<R>& p, const V4<R>& v,
+                                               const int A[3], double w)
+{
+    if (!B.damage || p.w < R(0)) return;
+    const double ke = 0.5 * P.M2[((int)p.w) & 1] * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+    if (!(ke > P.dmin)) return;
+    const double x = (double)p.x + (double)A[0] * P.a, y = (double)p.y + (double)A[1] * P.a,
+                 z = (double)p.z + (double)A[2] * P.a;
+    const int ix = (int)floor((x + P.dhalf) / P.dvox), iy = (int)floor((y + P.dhalf) / P.dvox),
+              iz = (int)floor(z / P.dvox);
+    const size_t n = (size_t)P.dn;
+    size_t cell = n * n * n;   // overflow
+    if (ix >= 0 && iy >= 0 && iz >= 0 && ix < P.dn && iy < P.dn && iz < P.dn) cell = ((size_t)ix * n + iy) * n + iz;
+    atomicAdd(&B.damage[cell], w * ke);
+}
 template <typename R> __device__ __forceinline__ bool is_active(const V4<R>& p) { return p.w >= R(0) && p.w < R(2); }
 template <typename R> __device__ __forceinline__ int species_of(const V4<R>& p) { return ((int)p.w) & 1; }
 
@@ -254,7 +276,7 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
                                       bool brute, int& overflow)
 {
     const V4<R> pi = W.pos[i];
-    uint16_t* out = W.nbr + (size_t)slot * REED_MAXNB;
+    uint16_t* out = W.nbr + (size_t)slot * maxnb(TT);
     int cnt = 0;
     const int na = P.na;
     auto consider = [&](int j) {
@@ -263,9 +285,10 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
         if (!is_present(pj)) return;
         const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
         if (dx * dx + dy * dy + dz * dz < H.rlist2) {
-            if (cnt < REED_MAXNB) out[cnt++] = (uint16_t)j;
+            if (cnt < maxnb(TT)) out[cnt++] = (uint16_t)j;
             else ++overflow;
-            if (!is_active(pj) && W.need_map[j] == REED_NO_SLOT) W.need_map[j] = (uint16_t)REED_PENDING;
+            if (TT == REED_TT_TERSOFF && !is_active(pj) && W.need_map[j] == REED_NO_SLOT)
+                W.need_map[j] = (uint16_t)REED_PENDING;
         }
     };
     if (brute || (W.flags[i] & 1)) {
@@ -385,13 +408,20 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
         S->active_count = nact_slots;
     }
     __syncthreads();
-    const bool brute = force_brute || S->out_ovf != 0;
+    // pair lists reach further than a - 2 REED_DISPLACED: search every atom
+    const bool brute = force_brute || S->out_ovf != 0 || TT == REED_TT_BUCKINGHAM;
     // lists of integrated atoms; their other neighbours become pending
     for (int k = threadIdx.x; k < nact_slots; k += blockDim.x) {
         const int i = W.slot_atom[k];
         W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, brute, overflow);
     }
     __syncthreads();
+    if constexpr (TT != REED_TT_TERSOFF) {
+        // pair potentials need lists of the integrated atoms only
+        if (threadIdx.x == 0) S->need_count = nact_slots;
+        __syncthreads();
+        return;
+    }
     // slots for the pending atoms, in atom order after the integrated ones
     int npend = 0;
     for (int i = i0; i < i1; ++i) npend += W.need_map[i] == REED_PENDING;
@@ -581,9 +611,10 @@ __device__ R pair_force(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& F
     const int m = W.nnb[k];
     const V4<R> pi = W.pos[i];
     const int si = species_of(pi);
+    const uint16_t* nb = W.nbr + (size_t)k * maxnb(TT);
     R E = R(0);
     for (int q = 0; q < m; ++q) {
-        const V4<R> pj = W.pos[W.nbr[(size_t)k * REED_MAXNB + q]];
+        const V4<R> pj = W.pos[nb[q]];
         R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
         R r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= H.b_rc2) continue;
@@ -1053,7 +1084,13 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             bool any_new = false;
             for (int i = tid; i < P.na; i += blockDim.x) {
                 V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
-                if (shift) any_new |= reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f);
+                if (shift) {
+                    const V4<R> p0 = p, v0 = v;
+                    if (reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f)) {
+                        any_new = true;
+                        deposit_damage<R>(P, B, p0, v0, S->Aold, ldexp(1.0, -S->ion.level));
+                    }
+                }
                 if (is_active(p)) {
                     ++wc.moved;
                     const R k = hdt * H.invM2[species_of(p)];
@@ -1160,6 +1197,15 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
         }
         // ---- track finished
         lap(PH_ADMIN);
+        if (B.damage) {
+            const int A[3] = {S->ion.A[0], S->ion.A[1], S->ion.A[2]};
+            const double wgt = ldexp(1.0, -S->ion.level);
+            for (int i = tid; i < P.na; i += blockDim.x) {
+                const V4<R> p = W.pos[i];
+                if (is_active(p)) deposit_damage<R>(P, B, p, W.vel[i], A, wgt);
+            }
+            __syncthreads();
+        }
         if (tid == 0) {
             if (S->status == REED_TRACK_FAILED) {
                 ++c_fail;

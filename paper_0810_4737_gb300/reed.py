@@ -50,7 +50,9 @@ class reed_run_opts(C.Structure):
                 ("ctas_per_sm", C.c_int32), ("record_tracks", C.c_int32), ("trace_tracks", C.c_int32),
                 ("trace_steps", C.c_int32), ("reserved", C.c_int32), ("record_capacity", C.c_int64),
                 ("stream", C.c_void_p), ("adaptive", C.c_int32), ("reserved2", C.c_int32),
-                ("epoch_size", C.c_int64), ("n_initial", C.c_int64), ("target_tracks", C.c_int64)]
+                ("epoch_size", C.c_int64), ("n_initial", C.c_int64), ("target_tracks", C.c_int64),
+                ("damage_n", C.c_int32), ("reserved3", C.c_int32), ("damage_voxel", C.c_double),
+                ("damage_min", C.c_double)]
 
 
 class reed_track_record(C.Structure):
@@ -79,7 +81,7 @@ class reed_stats_t(C.Structure):
 
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",
             "reed_reset", "reed_last_error", "reed_destroy", "reed_philox", "reed_cell_atoms", "reed_forces",
-            "reed_window_replay", "reed_run_static", "reed_thresholds"]
+            "reed_window_replay", "reed_run_static", "reed_thresholds", "reed_damage_map"]
 
 _LIB = None
 _D = C.POINTER(C.c_double)
@@ -116,6 +118,7 @@ def lib():
         L.reed_trace.argtypes = [vp, vp, vp, C.c_int, C.c_int]
         L.reed_reset.argtypes = [vp]
         L.reed_thresholds.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int)]
+        L.reed_damage_map.argtypes = [vp, vp, C.c_int, vp]
         L.reed_last_error.argtypes = [vp]
         L.reed_last_error.restype = C.c_char_p
         L.reed_destroy.argtypes = [vp]
@@ -174,7 +177,7 @@ def potentials_struct(w) -> reed_potentials:
 
 def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, record=True, record_capacity=0,
              trace_tracks=0, trace_steps=0, stream=None, adaptive=False, epoch_size=4096, n_initial=50,
-             target_tracks=0) -> reed_run_opts:
+             target_tracks=0, damage=True) -> reed_run_opts:
     o = reed_run_opts()
     o.dt_max_fs, o.dx_max, o.e_stop = w["dt_max_fs"], w["dx_max"], w["e_stop"]
     o.step_cap = int(w["step_cap"])
@@ -193,6 +196,8 @@ def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, reco
     o.stream = stream
     o.adaptive = 1 if adaptive else 0
     o.epoch_size, o.n_initial, o.target_tracks = epoch_size, n_initial, target_tracks
+    o.damage_n = int(w.get("damage_n", 0)) if damage else 0
+    o.damage_voxel, o.damage_min = float(w.get("damage_voxel", 10.0)), float(w.get("damage_min", 0.1))
     return o
 
 
@@ -247,6 +252,14 @@ def reed_thresholds(ctx, max_epochs=1024):
     if h.shape[0]:
         _check(lib().reed_thresholds(ctx, h.ctypes.data, h.shape[0], C.byref(n)), ctx)
     return h
+
+
+def reed_damage_map(ctx, n):
+    """(n, n, n) damage map (eV) and the energy deposited outside it."""
+    out = np.zeros((n, n, n))
+    ov = np.zeros(1)
+    _check(lib().reed_damage_map(ctx, out.ctypes.data, n, ov.ctypes.data), ctx)
+    return out, float(ov[0])
 
 
 def reed_reset(ctx):
@@ -307,7 +320,7 @@ def reed_run_static(w, n_ions, seed, hist_out_ptr, precision=PREC_MIXED, stream=
     dict describes target and run; hist_out_ptr is a device buffer of
     n_bins + 3 doubles owned by the caller.  Returns the stats dict."""
     sp = species_array(w)
-    o = run_opts(w, precision=precision, record=False, stream=stream, **kw)
+    o = run_opts(w, precision=precision, record=False, stream=stream, damage=False, **kw)
     st = reed_stats_t()
     ion = w["ion"]
     _check(lib().reed_run_static(C.byref(lattice_struct(w)), sp, len(w["species"]), C.byref(potentials_struct(w)),
@@ -354,6 +367,9 @@ class Reed:
 
     def thresholds(self):
         return reed_thresholds(self.ctx)
+
+    def damage_map(self):
+        return reed_damage_map(self.ctx, int(self.w["damage_n"]))
 
     def forces(self, ion_x, xyz, sp, precision=PREC_MIXED):
         ion = self.w["ion"]

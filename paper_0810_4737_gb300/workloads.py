@@ -81,6 +81,9 @@ _BASE = {
     "n_bins": 100,
     "bin_w": 2.0,
     "seed": 0,
+    "damage_n": 0,          # cumulative damage map: voxels per edge (0 = off)
+    "damage_voxel": 10.0,   # A
+    "damage_min": 0.1,      # eV: atoms below this kinetic energy deposit nothing
 }
 
 
@@ -99,7 +102,7 @@ WORKLOADS = {
     "ar30kev_ceo2_300k_buck": dict(
         _BASE, ion=AR40, energy=30000.0, n_ions=16384, lattice="fluorite", a=5.411, n=4,
         margin=0, sigma=0.076, species=[CE, O16], tt="buckingham", beam_mode="cone",
-        tilt=10.0, rot=(0.0, 360.0), n_bins=200, bin_w=5.0),
+        tilt=10.0, rot=(0.0, 360.0), n_bins=200, bin_w=5.0, damage_n=64),
     "b10kev_si_300k_adjoint": dict(
         _BASE, ion=B11, energy=10000.0, n_ions=16384, sigma=0.076, rot=(0.0, 45.0),
         n_bins=200, bin_w=10.0),

@@ -1,0 +1,101 @@
+"""Fluorite CeO2 with Buckingham target-target pairs, and the cumulative
+damage map, through the C ABI against the oracle.
+
+* Buckingham + ZBL-blend forces of a disordered fluorite block: 1e-5
+  relative (mixed) and 1e-10 (FP64);
+* the first 50 steps of Ar ions at 30 keV (cone beam, per-species
+  stopping) within 1e-4 A;
+* the damage map: energy deposited per ion and its depth distribution agree
+  with the oracle within statistics; deposits are non-negative and lie where
+  the ions went.
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_0810_4737_gb300.workloads import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_0810_4737_gb300 import build, reed
+    build.build()
+    return reed
+
+
+def _fluorite_block(O, w, seed, ion):
+    p = O.params(w)
+    a, n = w["a"], w["n"]
+    A = np.floor(ion / a + 0.5).astype(int)
+    xs, ss = [], []
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                x, s = O.cell_atoms(p, 7, *(A - n // 2 + np.array([i, j, k])))
+                xs.append(x)
+                ss.append(s)
+    rng = np.random.default_rng(seed)
+    X = np.vstack(xs)
+    return X + rng.normal(scale=0.1, size=X.shape), np.concatenate(ss)
+
+
+def _rel(fg, fo):
+    scale = np.sqrt(np.mean(np.sum(fo ** 2, axis=1)))
+    return np.max(np.linalg.norm(fg - fo, axis=1) / np.maximum(np.linalg.norm(fo, axis=1), 0.01 * scale))
+
+
+def test_buckingham_forces_match_oracle(R, O):
+    w = workload("ar30kev_ceo2_300k_buck", sigma=0.0)
+    p = O.params(w)
+    for seed, ion in [(1, np.array([3.1, 2.2, 9.3])), (2, np.array([0.4, 5.0, 12.1]))]:
+        X, S = _fluorite_block(O, w, seed, ion)
+        d = np.linalg.norm(X - ion, axis=1)
+        X[np.argmin(d)] = ion + np.array([0.3, -0.2, 0.1])
+        # a close O-O pair inside the ZBL blend
+        o = np.nonzero(S == 1)[0]
+        X[o[1]] = X[o[0]] + np.array([0.5, 0.4, 0.3])
+        Eo, fio, fao, _ = O.forces(p, ion, X, S)
+        with R.Reed(w) as ctx:
+            for prec, tol in ((1, 1e-10), (0, 1e-5)):
+                Eg, fig, fag, _ = ctx.forces(ion, X, S, precision=prec)
+                assert _rel(fag, fao) < tol, (prec, _rel(fag, fao))
+                assert np.linalg.norm(fig - fio) <= tol * np.linalg.norm(fio)
+                assert abs(Eg - Eo) <= 10 * tol * max(abs(Eo), 1.0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_first_50_steps_ceo2(R, O, prec):
+    w = workload("ar30kev_ceo2_300k_buck")
+    p = O.params(w)
+    n, steps = 4, 50
+    with R.Reed(w) as ctx:
+        rc = ctx.run(n_ions=n, seed=0, precision=prec, trace_tracks=n, trace_steps=steps)
+        traj, anc = ctx.trace(n, steps)
+    for t in range(n):
+        ref, ranc = O.trace(p, 0, t, steps)
+        k = ref.shape[0]
+        assert np.max(np.abs(traj[t, :k, :3] - ref[:, :3])) < 1e-4
+        assert np.array_equal(anc[t, :k], ranc)
+
+
+def test_damage_map_matches_oracle(R, O):
+    w = workload("b1kev_si_0k_zbl", sigma=0.076, rot=(0.0, 45.0), damage_n=32, damage_voxel=5.0)
+    n = 1024
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n, seed=8)
+        dg, og = ctx.damage_map()
+    ref = O.run(O.params(w), n, seed=8, threads=16)
+    do, oo = ref["damage"], ref["damage_overflow"]
+    assert np.all(dg >= 0)
+    tg, to = dg.sum() + og, do.sum() + oo
+    # energy deposited per ion: same physics, independent (chaotic) samples
+    assert abs(tg / to - 1) < 0.03, (tg, to)
+    # depth distribution of the deposited energy
+    zg, zo = dg.sum(axis=(0, 1)), do.sum(axis=(0, 1))
+    cg, co = np.cumsum(zg) / zg.sum(), np.cumsum(zo) / zo.sum()
+    assert np.max(np.abs(cg - co)) < 0.03
+    # lateral extent centred on the entry cell
+    xg = dg.sum(axis=(1, 2))
+    assert xg[:8].sum() < 0.05 * xg.sum() and xg[-8:].sum() < 0.05 * xg.sum()

@@ -210,3 +210,32 @@ def test_adaptive_run_converges_and_conserves(O):
     assert np.max(np.abs(th[-1][both] - th[-2][both]) / th[-1][both]) < 0.5
     total = r["hist"].sum() + r["under"] + r["over"] + r["back"] + r["w_trunc"]
     assert total == 800.0
+
+
+def test_damage_energy_balance(O):
+    """Free target atoms at 0 K: the ion's initial energy ends up in its final
+    kinetic energy, the final potential energy, electronic stopping, the
+    damage map (dropped cells), the kinetic energy below the deposit threshold
+    and the final window's kinetic energy (C15), up to the integrator's error
+    (KDK at dt = 0.05 A / v and the first-order drag-work estimate: < 1 %)."""
+    w = workload("b1kev_si_0k_zbl", damage_n=64)
+    p = O.params(w)
+    for tid in range(6):
+        e = O.track_energy(p, 0, tid)
+        rest = e["ke_ion"] + e["pe"] + e["e_elec"] + e["deposited"] + e["below_threshold"] + e["ke_window"]
+        assert abs(rest / e["E0"] - 1.0) < 1e-2, (tid, e)
+        assert e["deposited"] > 0.0
+
+
+def test_damage_map_totals(O):
+    w = workload("b1kev_si_0k_zbl", sigma=0.076, damage_n=32, damage_voxel=5.0,
+                 thresholds=[20.0, 40.0])
+    p = O.params(w)
+    r = O.run(p, 64, seed=1, threads=8)
+    d = r["damage"]
+    assert d.shape == (32, 32, 32)
+    assert np.all(d >= 0) and d.sum() > 0
+    # deposits lie at the depths the ions reached (z index below the deepest stop + a window)
+    zmax = r["records"]["z"].max()
+    iz = np.nonzero(d.sum(axis=(0, 1)))[0]
+    assert iz.max() * 5.0 <= zmax + 3 * 5.431 + 5.0

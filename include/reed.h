@@ -158,6 +158,16 @@ typedef struct {
     int32_t reserved3;
     double damage_voxel;       /* A */
     double damage_min;         /* eV */
+    /* Truncated-segment sensitivities (target model NONE, no cloning, records
+     * on): for every stopped track, dz_T/dtheta for theta = (s_e, s_loc,
+     * spline_c[0..5]) through its last adj_segment steps (the state
+     * adj_segment..adj_segment+adj_every-1 steps before the end held fixed),
+     * with dt, window moves and the drag's on/off frozen; checkpoints every
+     * adj_every steps (defaults 200 and 20). */
+    int32_t adjoint;
+    int32_t adj_segment;
+    int32_t adj_every;
+    int32_t reserved4;
 } reed_run_opts;
 
 /* Per-track result: the depth and weight of one finished track (Sec. 3, result messages). */
@@ -226,6 +236,24 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
  * n_bins must equal the tally's bin count.  Errors: REED_E_STATE (no run),
  * REED_E_ARG. */
 int reed_range_profile(reed_ctx* ctx, double* bins_out, int n_bins, double* extra3);
+
+/* Per-track sensitivities dz/dtheta (8 doubles per record, in record order;
+ * zero for tracks that did not stop) of adjoint runs: out (host or device)
+ * receives up to cap rows; *n_out (host) the number of rows kept. */
+int reed_track_grads(reed_ctx* ctx, double* out, int64_t cap, int64_t* n_out);
+
+/* Kernel-density range profile of the stopped tracks recorded since
+ * init/reset: p[b] = sum_i w_i N(z_b; z_i, sigma) / sum_i w_i at bin centres
+ * z_b = (b + 1/2) bin_width (A^-1); p_out host or device, n_bins doubles. */
+int reed_kde_profile(reed_ctx* ctx, double sigma, int n_bins, double bin_width, double* p_out);
+
+/* Gradient of a loss of that profile: dL_dtheta[8] (host) =
+ * sum_i (sum_b dL_dp[b] dp_b/dz_i) dz_i/dtheta, from the per-track
+ * sensitivities of an adjoint run; dL_dp host or device, n_bins doubles. */
+int reed_grad(reed_ctx* ctx, double sigma, int n_bins, double bin_width, const double* dL_dp, double* dL_dtheta);
+
+/* Set theta = (s_e, s_loc, spline_c[0..5]) of the context's potentials. */
+int reed_set_theta(reed_ctx* ctx, const double* theta8);
 
 /* Cumulative damage map of all runs since init/reset: out (host or device)
  * receives n^3 doubles (eV, index (ix n + iy) n + iz), overflow (may be

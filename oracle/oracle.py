@@ -122,6 +122,12 @@ def lib():
             L.o_run_adaptive.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_uint64, C.c_int, _D,
                                          C.POINTER(C.c_int64), _D, _D, C.c_int]
             L.o_run_adaptive.restype = C.c_int
+            L.o_pair_full.argtypes = [_P, C.c_double, C.c_double, _D, _D, _D, _D]
+            L.o_segment_tangent.argtypes = [_P, C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int64, _D]
+            L.o_segment_tangent.restype = C.c_int
+            L.o_segment_replay_theta.argtypes = [_P, C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int64, C.c_int,
+                                                 C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.o_segment_replay_theta.restype = C.c_double
             L.o_basis_count.argtypes = [C.c_int]
             L.o_basis_count.restype = C.c_int
             _LIB = L
@@ -363,3 +369,29 @@ def track_energy(p: Params, seed: int, track_id: int) -> dict:
         raise ValueError("needs a damage grid and <= 1024 bins")
     keys = ["E0", "ke_ion", "pe", "e_elec", "deposited", "below_threshold", "ke_window", "steps"]
     return dict(zip(keys, out.tolist()))
+
+
+def pair_full(p: Params, Z2: float, r: float):
+    """Ion-target pair: (U, dU/dr, d2U/dr2, d(dU/dr)/dc_k for k = 0..5)."""
+    U, dU, d2U = C.c_double(), C.c_double(), C.c_double()
+    dc = np.zeros(6)
+    lib().o_pair_full(C.byref(p), Z2, r, C.byref(U), C.byref(dU), C.byref(d2U), _dp(dc))
+    return U.value, dU.value, d2U.value, dc
+
+
+def segment_tangent(p: Params, seed: int, track_id: int, seg: int = 200, every: int = 20, cap: int = 2_000_000):
+    """Forward-mode dz_T/dtheta over the frozen last segment of a primary:
+    dict(z, T, s0, grad[8]) with theta = (s_e, s_loc, c_1..c_6)."""
+    out = np.zeros(11)
+    if lib().o_segment_tangent(C.byref(p), seed, track_id, seg, every, cap, _dp(out)) != 0:
+        raise ValueError("track did not stop")
+    return {"z": out[0], "T": int(out[1]), "s0": int(out[2]), "grad": out[3:].copy()}
+
+
+def segment_z(p: Params, seed: int, track_id: int, direction: int, delta: float, seg: int = 200, every: int = 20,
+              cap: int = 2_000_000):
+    """z_T of the frozen segment replayed with theta_direction += delta."""
+    T, s0 = C.c_int64(), C.c_int64()
+    z = lib().o_segment_replay_theta(C.byref(p), seed, track_id, seg, every, cap, direction, delta, C.byref(T),
+                                     C.byref(s0))
+    return z, T.value, s0.value

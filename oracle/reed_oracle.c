@@ -1257,3 +1257,307 @@ double o_ion_pair_energy(const o_params* P, double Z2, double r, double* dU)
 }
 double o_taper_export(double r, double rt, double rc, double* dS) { return o_taper(r, rt, rc, dS); }
 double o_tau_fs(void) { return O_TAU_FS; }
+
+/* ======================================================================== */
+/* Truncated-segment sensitivities (the adjoint workload).                  */
+/* reading: the final depth z_T of a track depends on theta = (s_e, s_loc,   */
+/* c_1..c_6) only through its last ~200 steps: the state at step s0 =        */
+/* 20 floor((T-200)/20) (0 for T < 200) is held fixed, and so are the step   */
+/* sizes, the window moves and which side of the surface the ion is on at   */
+/* each half kick.  dz_T/dtheta is propagated here by forward-mode tangents */
+/* in FP64; tests pin it with central finite differences of the same frozen */
+/* replay.                                                                   */
+/* ======================================================================== */
+
+static double o_bspline3_d2(double u)
+{
+    double au = fabs(u);
+    if (au >= 2.0) return 0.0;
+    if (au >= 1.0) return 2.0 - au;
+    return -2.0 + 3.0 * au;
+}
+
+/* Ion-target pair U(r) with dU/dr, d2U/dr2 and d(dU/dr)/dc_k (k = 0..5). */
+void o_pair_full(const o_params* P, double Z2, double r, double* U, double* dU, double* d2U, double* dUdc)
+{
+    const double k = P->Z1 * Z2 * O_E2;
+    double au = o_zbl_screen_length(P->Z1, Z2);
+    double x = r / au, phi = 0.0, dphi = 0.0, d2phi = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        double e = exp(-O_ZD[i] * x);
+        phi += O_ZC[i] * e;
+        dphi -= O_ZC[i] * O_ZD[i] * e;
+        d2phi += O_ZC[i] * O_ZD[i] * O_ZD[i] * e;
+    }
+    double V = k * phi / r;
+    double V1 = k * (dphi / (au * r) - phi / (r * r));
+    double V2 = k * (d2phi / (au * au * r) - 2.0 * dphi / (au * r * r) + 2.0 * phi / (r * r * r));
+    /* correction c(r) = sum c_i B_i(u_i), u_i = (ln r - ln r_i)/h */
+    double h = (log(O_KNOTS[5]) - log(O_KNOTS[0])) / 5.0;
+    double c = 0.0, c1 = 0.0, c2 = 0.0, Bk[6], B1k[6];
+    for (int i = 0; i < 6; ++i) {
+        double u = (log(r) - log(O_KNOTS[i])) / h, du;
+        double b = o_bspline3(u, &du);
+        double d2 = o_bspline3_d2(u);
+        Bk[i] = b;
+        B1k[i] = du / (h * r);                       /* dB_i/dr */
+        c += P->spline_c[i] * b;
+        c1 += P->spline_c[i] * du / (h * r);
+        c2 += P->spline_c[i] * (d2 / (h * h * r * r) - du / (h * r * r));
+    }
+    double E = exp(c);
+    double dS, S = o_taper(r, P->rt, P->rc, &dS);
+    double d2S = 0.0;
+    if (r > P->rt && r < P->rc) {
+        double w = P->rc - P->rt, t = (r - P->rt) / w;
+        d2S = (-60.0 * t + 180.0 * t * t - 120.0 * t * t * t) / (w * w);
+    }
+    *U = V * E * S;
+    *dU = V1 * E * S + V * E * c1 * S + V * E * dS;
+    *d2U = V2 * E * S + 2.0 * V1 * E * c1 * S + 2.0 * V1 * E * dS + V * E * (c1 * c1 + c2) * S +
+           2.0 * V * E * c1 * dS + V * E * d2S;
+    for (int i = 0; i < 6; ++i) dUdc[i] = Bk[i] * (*dU) + V * E * S * B1k[i];
+}
+
+/* per-step record of the frozen quantities */
+typedef struct {
+    double dt;
+    int A[3];        /* anchor after the step */
+    int on1, on2;    /* drag active at the first / second half kick */
+} o_segstep;
+
+/* Conservative forces and, for one tangent direction, their derivative:
+ * dF = J(x) dx + dF/dtheta_dir.  dir: 0 s_e, 1 s_loc (no effect on F),
+ * 2..7 spline c_{dir-2}; dir < 0: no parameter term.  Also returns rho and
+ * its gradient contracted with dx (drho), and the d rho/d x_ion, d rho/d x_j
+ * needed by the drag. */
+static void o_forces_tangent(const o_params* P, const double* xi, int n, const double* x, const int* sp,
+                             const double* dxi, const double* dx, int dir, double* fi, double* f, double* dfi,
+                             double* df, double* rho, double* drho)
+{
+    for (int d = 0; d < 3; ++d) { fi[d] = 0.0; dfi[d] = 0.0; }
+    for (int j = 0; j < 3 * n; ++j) { f[j] = 0.0; df[j] = 0.0; }
+    *rho = 0.0;
+    *drho = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double rv[3], r = o_dist(xi, &x[3 * j], rv);
+        if (r >= P->rc) continue;
+        double U, dU, d2U, dUdc[6];
+        o_pair_full(P, P->Z2[sp[j]], r, &U, &dU, &d2U, dUdc);
+        double u[3] = {rv[0] / r, rv[1] / r, rv[2] / r};
+        /* relative tangent */
+        double q[3] = {dx[3 * j] - dxi[0], dx[3 * j + 1] - dxi[1], dx[3 * j + 2] - dxi[2]};
+        double uq = u[0] * q[0] + u[1] * q[1] + u[2] * q[2];
+        for (int d = 0; d < 3; ++d) {
+            f[3 * j + d] -= dU * u[d];
+            fi[d] += dU * u[d];
+            /* K q, K = d2U u u^T + (dU/r)(I - u u^T) */
+            double Kq = d2U * u[d] * uq + dU / r * (q[d] - u[d] * uq);
+            double pth = (dir >= 2) ? dUdc[dir - 2] * u[d] : 0.0;
+            df[3 * j + d] -= Kq + pth;
+            dfi[d] += Kq + pth;
+        }
+        double dS, S = o_taper(r, P->rt, P->rc, &dS);
+        double e = exp(-r / P->lam_loc);
+        *rho += S * e;
+        *drho += (dS - S / P->lam_loc) * e * uq;
+    }
+}
+
+/* Run primary id; record per-step frozen quantities (steps, up to cap).
+ * Returns the number of steps T (or -1 if the track did not stop). */
+static int64_t o_seg_record(const o_params* P, uint64_t seed, uint64_t id, o_segstep* rec, int64_t cap)
+{
+    o_params Q = *P;
+    Q.nthr = 0;
+    o_consts K;
+    o_consts_init(&Q, &K);
+    o_ion I;
+    o_win W;
+    o_win_alloc(&W, o_window_capacity(&Q));
+    o_launch(&Q, seed, id, &I);
+    o_window_init(&Q, &W, &I, I.key);
+    o_forces(&Q, I.x, 1, W.n, W.x, W.sp, I.f, W.f, &I.rho);
+    int st = O_ALIVE;
+    int64_t s = 0;
+    while (st == O_ALIVE) {
+        int on1 = I.x[2] >= 0.0, moved;
+        double t0 = I.t;
+        o_step(&Q, &K, &I, &W, I.key, 0.0, 1, &moved, NULL);
+        if (s < cap) {
+            rec[s].dt = I.t - t0;
+            rec[s].A[0] = W.A[0]; rec[s].A[1] = W.A[1]; rec[s].A[2] = W.A[2];
+            rec[s].on1 = on1;
+            rec[s].on2 = I.x[2] >= 0.0;
+        }
+        ++s;
+        st = o_check(&Q, &I);
+    }
+    o_win_free(&W);
+    return st == O_STOPPED ? s : -1;
+}
+
+/* Frozen replay of steps s0..T-1 with parameters Pt (theta may differ from
+ * the recording's), optionally with one tangent direction.  The state at s0
+ * is produced by re-running the nominal track Pn from its launch.  Returns
+ * z_T; *dz gets the tangent dz_T/dtheta_dir (dir >= 0). */
+static double o_seg_replay(const o_params* Pn, const o_params* Pt, uint64_t seed, uint64_t id, const o_segstep* rec,
+                           int64_t T, int64_t s0, int dir, double* dz)
+{
+    o_params Qn = *Pn, Qt = *Pt;
+    Qn.nthr = Qt.nthr = 0;
+    o_consts Kn, Kt;
+    o_consts_init(&Qn, &Kn);
+    o_consts_init(&Qt, &Kt);
+    double g0 = o_gamma_ls(&Qt) / (Qt.s_e != 0.0 ? Qt.s_e : 1.0);   /* gamma without the s_e factor */
+    if (Qt.s_e == 0.0) { o_params Q1 = Qt; Q1.s_e = 1.0; g0 = o_gamma_ls(&Q1); }
+    double rho0 = o_rho0(&Qt);
+    o_ion I;
+    o_win W;
+    int cap = o_window_capacity(&Qn);
+    o_win_alloc(&W, cap);
+    o_launch(&Qn, seed, id, &I);
+    o_window_init(&Qn, &W, &I, I.key);
+    o_forces(&Qn, I.x, 1, W.n, W.x, W.sp, I.f, W.f, &I.rho);
+    for (int64_t s = 0; s < s0; ++s) {
+        int moved;
+        o_step(&Qn, &Kn, &I, &W, I.key, 0.0, 1, &moved, NULL);
+    }
+    /* tangents (zero at s0: the state there is held fixed); kept per window
+     * atom by its (cell, basis) identity through window moves */
+    double *dx = (double*)calloc(3 * (size_t)cap, sizeof(double)), *dv = (double*)calloc(3 * (size_t)cap, sizeof(double));
+    double *ndx = (double*)calloc(3 * (size_t)cap, sizeof(double)), *ndv = (double*)calloc(3 * (size_t)cap, sizeof(double));
+    double dxi[3] = {0, 0, 0}, dvi[3] = {0, 0, 0};
+    double *f = (double*)calloc(3 * (size_t)cap, sizeof(double)), *df = (double*)calloc(3 * (size_t)cap, sizeof(double));
+    double fi[3], dfi[3], rho, drho;
+    /* forces at the start of the segment with the replay's parameters */
+    o_forces_tangent(&Qt, I.x, W.n, W.x, W.sp, dxi, dx, dir, fi, f, dfi, df, &rho, &drho);
+    for (int64_t s = s0; s < T; ++s) {
+        const o_segstep* r = &rec[s];
+        double dt = r->dt, h = 0.5 * dt;
+        /* --- first half kick with drag at (v, x) */
+        double kf = r->on1 ? Qt.s_e * g0 * (1.0 + Qt.s_loc * (rho / rho0 - 1.0)) : 0.0;
+        double dk = 0.0;
+        if (r->on1 && dir >= 0) {
+            dk = Qt.s_e * g0 * Qt.s_loc / rho0 * drho;
+            if (dir == 0) dk += g0 * (1.0 + Qt.s_loc * (rho / rho0 - 1.0));
+            if (dir == 1) dk += Qt.s_e * g0 * (rho / rho0 - 1.0);
+        }
+        for (int d = 0; d < 3; ++d) {
+            double fe = -kf * I.v[d];
+            double dfe = -kf * dvi[d] - dk * I.v[d];
+            I.v[d] += h / Qt.M1 * (fi[d] + fe);
+            dvi[d] += h / Qt.M1 * (dfi[d] + dfe);
+        }
+        for (int j = 0; j < W.n; ++j) {
+            if (!W.act[j]) continue;
+            double m = Qt.M2[W.sp[j]];
+            for (int d = 0; d < 3; ++d) {
+                W.v[3 * j + d] += h / m * f[3 * j + d];
+                dv[3 * j + d] += h / m * df[3 * j + d];
+            }
+        }
+        /* --- drift */
+        for (int d = 0; d < 3; ++d) { I.x[d] += dt * I.v[d]; dxi[d] += dt * dvi[d]; }
+        for (int j = 0; j < W.n; ++j) {
+            if (!W.act[j]) continue;
+            for (int d = 0; d < 3; ++d) { W.x[3 * j + d] += dt * W.v[3 * j + d]; dx[3 * j + d] += dt * dv[3 * j + d]; }
+        }
+        /* --- frozen window move: anchor from the record */
+        if (r->A[0] != W.A[0] || r->A[1] != W.A[1] || r->A[2] != W.A[2]) {
+            /* remember tangents by atom identity, move the window, restore */
+            int n_old = W.n;
+            int* ids = (int*)malloc(sizeof(int) * 4 * (size_t)n_old);
+            for (int j = 0; j < n_old; ++j) {
+                ids[4 * j] = W.cell[3 * j]; ids[4 * j + 1] = W.cell[3 * j + 1]; ids[4 * j + 2] = W.cell[3 * j + 2];
+                ids[4 * j + 3] = W.bas[j];
+                for (int d = 0; d < 3; ++d) { ndx[3 * j + d] = dx[3 * j + d]; ndv[3 * j + d] = dv[3 * j + d]; }
+            }
+            o_ion Ia = I;
+            Ia.x[0] = (r->A[0] - (Qn.n % 2 == 0 ? 0.5 : 0.0) + 0.5) * Qn.a;   /* a point inside the recorded anchor cell */
+            Ia.x[1] = (r->A[1] - (Qn.n % 2 == 0 ? 0.5 : 0.0) + 0.5) * Qn.a;
+            Ia.x[2] = (r->A[2] - (Qn.n % 2 == 0 ? 0.5 : 0.0) + 0.5) * Qn.a;
+            o_window_update(&Qn, &W, &Ia, I.key, NULL);
+            for (int j = 0; j < W.n; ++j) {
+                int found = -1;
+                for (int q = 0; q < n_old; ++q)
+                    if (ids[4 * q] == W.cell[3 * j] && ids[4 * q + 1] == W.cell[3 * j + 1] &&
+                        ids[4 * q + 2] == W.cell[3 * j + 2] && ids[4 * q + 3] == W.bas[j]) { found = q; break; }
+                for (int d = 0; d < 3; ++d) {
+                    dx[3 * j + d] = found >= 0 ? ndx[3 * found + d] : 0.0;
+                    dv[3 * j + d] = found >= 0 ? ndv[3 * found + d] : 0.0;
+                }
+            }
+            free(ids);
+        }
+        /* --- forces at the new positions */
+        o_forces_tangent(&Qt, I.x, W.n, W.x, W.sp, dxi, dx, dir, fi, f, dfi, df, &rho, &drho);
+        /* --- second half kick with drag at (v_half, x') */
+        kf = r->on2 ? Qt.s_e * g0 * (1.0 + Qt.s_loc * (rho / rho0 - 1.0)) : 0.0;
+        dk = 0.0;
+        if (r->on2 && dir >= 0) {
+            dk = Qt.s_e * g0 * Qt.s_loc / rho0 * drho;
+            if (dir == 0) dk += g0 * (1.0 + Qt.s_loc * (rho / rho0 - 1.0));
+            if (dir == 1) dk += Qt.s_e * g0 * (rho / rho0 - 1.0);
+        }
+        for (int d = 0; d < 3; ++d) {
+            double fe = -kf * I.v[d];
+            double dfe = -kf * dvi[d] - dk * I.v[d];
+            I.v[d] += h / Qt.M1 * (fi[d] + fe);
+            dvi[d] += h / Qt.M1 * (dfi[d] + dfe);
+        }
+        for (int j = 0; j < W.n; ++j) {
+            if (!W.act[j]) continue;
+            double m = Qt.M2[W.sp[j]];
+            for (int d = 0; d < 3; ++d) {
+                W.v[3 * j + d] += h / m * f[3 * j + d];
+                dv[3 * j + d] += h / m * df[3 * j + d];
+            }
+        }
+    }
+    double z = I.x[2];
+    if (dz) *dz = dxi[2];
+    free(dx); free(dv); free(ndx); free(ndv); free(f); free(df);
+    o_win_free(&W);
+    return z;
+}
+
+/* Segment sensitivities of primary id: out[0] = z_T, out[1] = T, out[2] =
+ * s0, out[3..10] = dz_T/dtheta (forward-mode tangents).  Returns 0, or -1
+ * if the track did not stop within cap steps. */
+int o_segment_tangent(const o_params* P, uint64_t seed, uint64_t id, int seg, int every, int64_t cap, double* out)
+{
+    o_segstep* rec = (o_segstep*)calloc((size_t)cap, sizeof(o_segstep));
+    int64_t T = o_seg_record(P, seed, id, rec, cap);
+    if (T < 0 || T > cap) { free(rec); return -1; }
+    int64_t s0 = T > seg ? (int64_t)every * ((T - seg) / every) : 0;
+    out[1] = (double)T;
+    out[2] = (double)s0;
+    for (int dir = 0; dir < 8; ++dir) {
+        double dz;
+        out[0] = o_seg_replay(P, P, seed, id, rec, T, s0, dir, &dz);
+        out[3 + dir] = dz;
+    }
+    free(rec);
+    return 0;
+}
+
+/* z_T of the frozen segment replayed with parameter theta_dir changed by
+ * delta (for finite differences).  Returns z_T; *T_out, *s0_out set. */
+double o_segment_replay_theta(const o_params* P, uint64_t seed, uint64_t id, int seg, int every, int64_t cap, int dir,
+                              double delta, int64_t* T_out, int64_t* s0_out)
+{
+    o_segstep* rec = (o_segstep*)calloc((size_t)cap, sizeof(o_segstep));
+    int64_t T = o_seg_record(P, seed, id, rec, cap);
+    if (T < 0 || T > cap) { free(rec); return NAN; }
+    int64_t s0 = T > seg ? (int64_t)every * ((T - seg) / every) : 0;
+    o_params Pt = *P;
+    if (dir == 0) Pt.s_e += delta;
+    else if (dir == 1) Pt.s_loc += delta;
+    else Pt.spline_c[dir - 2] += delta;
+    double z = o_seg_replay(P, &Pt, seed, id, rec, T, s0, -1, NULL);
+    free(rec);
+    *T_out = T;
+    *s0_out = s0;
+    return z;
+}

@@ -38,6 +38,8 @@ const double kFluorite[12][3] = {{0, 0, 0},       {0, .5, .5},     {.5, 0, .5}, 
 const double kKnots[6] = {0.2, 0.35, 0.6, 1.0, 1.7, 3.0};
 
 const double kSkin = 0.3;   // neighbour-list skin, A
+#define REED_NTHETA_HOST 8
+#define REED_STEP_RING_HOST 256
 
 double screen_inv(double Z1, double Z2) { return (std::pow(Z1, 0.23) + std::pow(Z2, 0.23)) / (0.8854 * REED_BOHR); }
 
@@ -72,6 +74,13 @@ struct reed_ctx {
     // scratch for diagnostics
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // truncated-segment sensitivities
+    double* d_grads = nullptr;
+    long long grads_cap = 0;
+    unsigned char* d_adj = nullptr;
+    size_t adj_bytes = 0;
+    double* d_kde = nullptr;       // scratch for the profile / gradient kernels
+    size_t kde_bytes = 0;
     // cumulative damage map (fixed by the first run that asks for it)
     double* d_damage = nullptr;
     int dn = 0;
@@ -109,6 +118,8 @@ int fail(reed_ctx* c, int code, const char* fmt, ...)
             return fail(ctx, e_ == cudaErrorMemoryAllocation ? REED_E_NOMEM : REED_E_CUDA,         \
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);      \
     } while (0)
+
+double lindhard_gamma_unit(const reed_ctx* ctx, double Z1, double M1);
 
 template <typename T> void fill_hot(HotParams<T>& h, const DevParams& P, const reed_ctx* ctx, double skin)
 {
@@ -176,6 +187,7 @@ template <typename T> void fill_hot(HotParams<T>& h, const DevParams& P, const r
     h.M1 = (T)P.M1;
     h.invM1 = (T)P.invM1;
     h.gamma = (T)P.gamma;
+    h.gamma0 = (T)lindhard_gamma_unit(ctx, P.Z1, P.M1);
     h.s_loc = (T)P.s_loc;
     h.rho0_inv = (T)P.rho0_inv;
     h.anchor_lo = (T)(-P.anchor_shift * P.a);
@@ -187,7 +199,15 @@ int basis_count(int kind) { return kind == REED_LATTICE_FLUORITE ? 12 : 8; }
 // Lindhard-Scharff electronic stopping: S = k sqrt(E), k = 1.212 Z1^(7/6) Z2 /
 // ((Z1^(2/3) + Z2^(2/3))^(3/2) sqrt(M1)) eV^(1/2) A^2; as a drag on the
 // velocity, gamma = N k sqrt(M1/2) summed over target species.
+double lindhard_gamma_unit(const reed_ctx* ctx, double Z1, double M1);
+
 double lindhard_gamma(const reed_ctx* ctx, double Z1, double M1)
+{
+    return ctx->pot.s_e * lindhard_gamma_unit(ctx, Z1, M1);
+}
+
+// the same without the stopping scale s_e
+double lindhard_gamma_unit(const reed_ctx* ctx, double Z1, double M1)
 {
     const double vol = ctx->lat.a * ctx->lat.a * ctx->lat.a;
     double g = 0.0;
@@ -198,7 +218,7 @@ double lindhard_gamma(const reed_ctx* ctx, double Z1, double M1)
         double k = 1.212 * std::pow(Z1, 7.0 / 6.0) * Z2 / (den * std::sqrt(M1));
         g += count / vol * k;
     }
-    return ctx->pot.s_e * g * std::sqrt(M1 / 2.0);
+    return g * std::sqrt(M1 / 2.0);
 }
 
 // Rows of Tersoff bond storage: atoms of a perfect bulk window that are
@@ -395,6 +415,73 @@ static __global__ void update_thresholds_kernel(const double* __restrict__ hist,
         for (int k = 0; k < REED_MAX_THR; ++k) history_row[k] = k < nthr ? thr[k] : 0.0;
 }
 
+
+// ---------------------------------------------------------------------------
+// Kernel-density profile of the recorded stopped tracks and its gradient
+// (the adjoint workload's loss interface).  Deterministic: fixed summation
+// orders, no atomics.
+// ---------------------------------------------------------------------------
+static __global__ void kde_weight_kernel(const reed_track_record* __restrict__ rec, long long n, double* __restrict__ wsum)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (long long i = 0; i < n; ++i)
+        if (rec[i].status == REED_TRACK_STOPPED) s += ldexp(1.0, -rec[i].level);
+    *wsum = s;
+}
+
+static __global__ void kde_profile_kernel(const reed_track_record* __restrict__ rec, long long n, const double* wsum,
+                                          double sigma, int nb, double bw, double* __restrict__ p)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const double zb = (b + 0.5) * bw, c = 1.0 / (sqrt(2.0 * REED_PI) * sigma), i2s = 0.5 / (sigma * sigma);
+    double acc = 0.0;
+    for (long long i = 0; i < n; ++i) {
+        if (rec[i].status != REED_TRACK_STOPPED) continue;
+        const double d = zb - rec[i].z;
+        acc += ldexp(1.0, -rec[i].level) * exp(-d * d * i2s);
+    }
+    p[b] = *wsum > 0.0 ? acc * c / *wsum : 0.0;
+}
+
+// per-record contributions dL/dz_i * dz_i/dtheta, reduced per block in order
+static __global__ void kde_grad_kernel(const reed_track_record* __restrict__ rec, const double* __restrict__ grads,
+                                       long long n, const double* wsum, double sigma, int nb, double bw,
+                                       const double* __restrict__ dLdp, double* __restrict__ part)
+{
+    __shared__ double red[256][REED_NTHETA_HOST];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double g[REED_NTHETA_HOST] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (i < n && rec[i].status == REED_TRACK_STOPPED && *wsum > 0.0) {
+        const double c = 1.0 / (sqrt(2.0 * REED_PI) * sigma), is2 = 1.0 / (sigma * sigma);
+        const double w = ldexp(1.0, -rec[i].level) / *wsum, z = rec[i].z;
+        double dz = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double d = (b + 0.5) * bw - z;
+            dz += dLdp[b] * w * c * exp(-0.5 * d * d * is2) * d * is2;
+        }
+        for (int k = 0; k < REED_NTHETA_HOST; ++k) g[k] = dz * grads[(size_t)i * REED_NTHETA_HOST + k];
+    }
+    for (int k = 0; k < REED_NTHETA_HOST; ++k) red[threadIdx.x][k] = g[k];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < REED_NTHETA_HOST; ++k) red[threadIdx.x][k] += red[threadIdx.x + o][k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < REED_NTHETA_HOST; ++k) part[(size_t)blockIdx.x * REED_NTHETA_HOST + k] = red[0][k];
+}
+
+static __global__ void sum_parts_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out)
+{
+    if (threadIdx.x >= REED_NTHETA_HOST || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * REED_NTHETA_HOST + threadIdx.x];
+    out[threadIdx.x] = s;
+}
+
 extern "C" {
 
 int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, int n_species,
@@ -530,7 +617,21 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     // launch shape
     const int tt = P.tt;
     const bool f64 = o.precision == REED_PREC_FP64;
-    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap) : reed_f32::smem_bytes(tt, P.na, P.bond_cap);
+    // truncated-segment sensitivities
+    if (o.adjoint) {
+        if (tt != REED_TT_NONE || P.nthr > 0 || o.adaptive || !o.record_tracks)
+            return fail(ctx, REED_E_ARG, "adjoint runs need target model NONE, no cloning and record_tracks");
+        const int seg = o.adj_segment > 0 ? o.adj_segment : 200, every = o.adj_every > 0 ? o.adj_every : 20;
+        if (seg % every != 0 || seg + every > REED_STEP_RING_HOST)
+            return fail(ctx, REED_E_ARG, "adj_segment must be a multiple of adj_every and adj_segment + adj_every <= %d",
+                        REED_STEP_RING_HOST);
+        P.adjoint = 1;
+        P.adj_seg = seg;
+        P.adj_every = every;
+        P.adj_nck = seg / every + 1;
+    }
+    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap, P.adjoint)
+                            : reed_f32::smem_bytes(tt, P.na, P.bond_cap, P.adjoint);
     if (smem > ctx->smem_optin)
         return fail(ctx, REED_E_SMEM, "window of %d atoms needs %zu B of shared memory (max %zu)", P.na, smem,
                     ctx->smem_optin);
@@ -570,6 +671,22 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     B.thr = ctx->d_thr;
     B.finished = ctx->d_finished;
     B.damage = o.damage_n > 0 ? ctx->d_damage : nullptr;
+    if (P.adjoint) {
+        if (!ctx->d_grads || ctx->grads_cap < ctx->rec_cap) {
+            if ((rc = dev_alloc(ctx, &ctx->d_grads, sizeof(double) * REED_NTHETA_HOST * (size_t)ctx->rec_cap))) return rc;
+            CK(cudaMemset(ctx->d_grads, 0, sizeof(double) * REED_NTHETA_HOST * (size_t)ctx->rec_cap));
+            ctx->grads_cap = ctx->rec_cap;
+        }
+        const size_t per = f64 ? reed_f64::adj_scratch_bytes(P, B.entry_bytes) : reed_f32::adj_scratch_bytes(P, B.entry_bytes);
+        const size_t need = per * (size_t)L.grid;
+        if (need > ctx->adj_bytes) {
+            if ((rc = dev_alloc(ctx, &ctx->d_adj, need))) return rc;
+            ctx->adj_bytes = need;
+        }
+        B.adj = ctx->d_adj;
+        B.adj_stride = per;
+        B.grads = ctx->d_grads;
+    }
     P.stop_after = o.target_tracks;
 
     // epochs: one launch, or (adaptive) unenhanced primaries followed by
@@ -749,6 +866,86 @@ int reed_trace(reed_ctx* ctx, double* traj, int32_t* anchors, int n_tracks, int 
     return REED_OK;
 }
 
+int reed_track_grads(reed_ctx* ctx, double* out, int64_t cap, int64_t* n_out)
+{
+    if (!ctx || !n_out || cap < 0) return REED_E_ARG;
+    if (!ctx->d_grads) return fail(ctx, REED_E_STATE, "no adjoint run since init/reset");
+    unsigned long long n = 0;
+    CK(cudaMemcpy(&n, ctx->d_rec_count, sizeof(n), cudaMemcpyDeviceToHost));
+    const int64_t kept = std::min<int64_t>((int64_t)n, ctx->rec_cap);
+    const int64_t m = std::min<int64_t>(kept, cap);
+    if (m > 0 && out) CK(cudaMemcpy(out, ctx->d_grads, sizeof(double) * REED_NTHETA_HOST * m, cudaMemcpyDefault));
+    *n_out = kept;
+    return REED_OK;
+}
+
+namespace {
+int kde_prepare(reed_ctx* ctx, int n_bins, long long* nrec, double** wsum, double** part, int* nblk)
+{
+    if (!ctx->d_records) return fail(ctx, REED_E_STATE, "no recorded tracks since init/reset");
+    unsigned long long n = 0;
+    CK(cudaMemcpy(&n, ctx->d_rec_count, sizeof(n), cudaMemcpyDeviceToHost));
+    *nrec = std::min<long long>((long long)n, ctx->rec_cap);
+    *nblk = (int)((*nrec + 255) / 256);
+    const size_t need = sizeof(double) * (8 + 2 * (size_t)n_bins + REED_NTHETA_HOST * (size_t)std::max(*nblk, 1) + 8);
+    if (need > ctx->kde_bytes) {
+        if (ctx->d_kde) cudaFree(ctx->d_kde);
+        ctx->d_kde = nullptr;
+        ctx->kde_bytes = 0;
+        CK(cudaMalloc((void**)&ctx->d_kde, need));
+        ctx->kde_bytes = need;
+    }
+    *wsum = ctx->d_kde;
+    *part = ctx->d_kde + 8 + 2 * (size_t)n_bins;
+    return REED_OK;
+}
+}  // namespace
+
+int reed_kde_profile(reed_ctx* ctx, double sigma, int n_bins, double bin_width, double* p_out)
+{
+    if (!ctx || !p_out || n_bins < 1 || !(sigma > 0) || !(bin_width > 0)) return REED_E_ARG;
+    long long n;
+    double *wsum, *part;
+    int nblk, rc;
+    if ((rc = kde_prepare(ctx, n_bins, &n, &wsum, &part, &nblk))) return rc;
+    double* dp = ctx->d_kde + 8;
+    kde_weight_kernel<<<1, 1>>>(ctx->d_records, n, wsum);
+    kde_profile_kernel<<<(n_bins + 127) / 128, 128>>>(ctx->d_records, n, wsum, sigma, n_bins, bin_width, dp);
+    CK(cudaGetLastError());
+    CK(cudaMemcpy(p_out, dp, sizeof(double) * n_bins, cudaMemcpyDefault));
+    return REED_OK;
+}
+
+int reed_grad(reed_ctx* ctx, double sigma, int n_bins, double bin_width, const double* dL_dp, double* dL_dtheta)
+{
+    if (!ctx || !dL_dp || !dL_dtheta || n_bins < 1 || !(sigma > 0) || !(bin_width > 0)) return REED_E_ARG;
+    if (!ctx->d_grads) return fail(ctx, REED_E_STATE, "no adjoint run since init/reset");
+    long long n;
+    double *wsum, *part;
+    int nblk, rc;
+    if ((rc = kde_prepare(ctx, n_bins, &n, &wsum, &part, &nblk))) return rc;
+    double* dl = ctx->d_kde + 8 + n_bins;
+    CK(cudaMemcpy(dl, dL_dp, sizeof(double) * n_bins, cudaMemcpyDefault));
+    kde_weight_kernel<<<1, 1>>>(ctx->d_records, n, wsum);
+    if (nblk > 0)
+        kde_grad_kernel<<<nblk, 256>>>(ctx->d_records, ctx->d_grads, n, wsum, sigma, n_bins, bin_width, dl, part);
+    double* out = part + (size_t)REED_NTHETA_HOST * std::max(nblk, 1);
+    if (nblk > 0) sum_parts_kernel<<<1, 32>>>(part, nblk, out);
+    else CK(cudaMemset(out, 0, sizeof(double) * REED_NTHETA_HOST));
+    CK(cudaGetLastError());
+    CK(cudaMemcpy(dL_dtheta, out, sizeof(double) * REED_NTHETA_HOST, cudaMemcpyDefault));
+    return REED_OK;
+}
+
+int reed_set_theta(reed_ctx* ctx, const double* theta8)
+{
+    if (!ctx || !theta8) return REED_E_ARG;
+    ctx->pot.s_e = theta8[0];
+    ctx->pot.s_loc = theta8[1];
+    for (int i = 0; i < 6; ++i) ctx->pot.spline_c[i] = theta8[2 + i];
+    return REED_OK;
+}
+
 int reed_damage_map(reed_ctx* ctx, double* out, int n, double* overflow)
 {
     if (!ctx || !out) return REED_E_ARG;
@@ -781,6 +978,9 @@ int reed_reset(reed_ctx* ctx)
     if (ctx->d_damage) cudaFree(ctx->d_damage);
     ctx->d_damage = nullptr;
     ctx->dn = 0;
+    if (ctx->d_grads) cudaFree(ctx->d_grads);
+    ctx->d_grads = nullptr;
+    ctx->grads_cap = 0;
     CK(cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT));
     CK(cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4));
     CK(cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long)));
@@ -794,7 +994,8 @@ void reed_destroy(reed_ctx* ctx)
     if (!ctx) return;
     void* ptrs[] = {ctx->d_hist, ctx->d_counters, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
                     ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch,
-                    ctx->d_thr, ctx->d_thr_hist, ctx->d_finished, ctx->d_damage};
+                    ctx->d_thr, ctx->d_thr_hist, ctx->d_finished, ctx->d_damage, ctx->d_grads,
+                    ctx->d_adj, ctx->d_kde};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1045,6 +1246,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
         return fail(nullptr, REED_E_ARG, "reed_run_static keeps no per-track records or traces");
     if (o.adaptive) return fail(nullptr, REED_E_ARG, "reed_run_static runs fixed cloning depths only");
     if (o.damage_n) return fail(nullptr, REED_E_ARG, "reed_run_static keeps no damage map");
+    if (o.adjoint) return fail(nullptr, REED_E_ARG, "reed_run_static computes no sensitivities");
 
     // device parameters from a host-only description of the target
     reed_ctx desc;

@@ -54,7 +54,7 @@ template <typename R> struct HotParams {
     // Buckingham
     R bA[3], brho_inv[3], bC[3], b_lo, b_binvw, b_rt, b_rinvw, b_rc2, b_zk[3], b_zia[3];
     // ion step
-    R dt_max, dx_max, e_stop, M1, invM1, gamma, s_loc, rho0_inv, anchor_lo, anchor_hi;
+    R dt_max, dx_max, e_stop, M1, invM1, gamma, gamma0, s_loc, rho0_inv, anchor_lo, anchor_hi;
 };
 
 // Everything a launch needs, passed by value (__grid_constant__).
@@ -98,6 +98,8 @@ struct DevParams {
     // cumulative damage map: dn^3 voxels of dvox, origin (-dhalf, -dhalf, 0)
     int dn;
     double dvox, dhalf, dmin;
+    // truncated-segment adjoint: segment length, checkpoint spacing, ring size
+    int adjoint, adj_seg, adj_every, adj_nck;
     long long stop_after;              // stop handing out primaries after this many tracks (0: never)
     // tallies
     int nbins;
@@ -125,6 +127,9 @@ struct DevBuf {
     int* status;                    // [0] OR of error bits
     const double* thr;              // cloning depths of this launch (adaptive epochs)
     double* damage;                 // dn^3 + 1 (overflow) voxels, or null
+    unsigned char* adj;             // per-CTA adjoint scratch (checkpoints, steps, block states)
+    size_t adj_stride;
+    double* grads;                  // 8 per track record: dz/dtheta
     unsigned long long* finished;   // tracks finished in this run (stop rule)
 };
 

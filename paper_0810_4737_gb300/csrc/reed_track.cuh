@@ -31,7 +31,7 @@
 #include "reed_physics.cuh"
 
 enum { SRC_NONE = 0, SRC_PRIMARY = 1, SRC_CLONE = 2 };
-enum { EV_NONE = 0, EV_END = 1, EV_CLONE = 2 };
+enum { EV_NONE = 0, EV_END = 1, EV_CLONE = 2, EV_CKPT = 3 };
 
 // Ion state as stored in shared memory and in clone records.  Position,
 // time and the energy given to electronic stopping are FP64 accumulators;
@@ -55,6 +55,12 @@ template <typename R> struct TrackShared {
     R zthr, zback, zsurf; // next cloning depth, backscatter plane, surface in the anchor frame
     double thr[REED_MAX_THR];  // this track's cloning depths (frozen while it runs)
     int nthr;
+    // adjoint workspace
+    int on1, on2;
+    long long rec_index;
+    R xbi[3], vbi[3], ubi[3], vh[3], irel[3], vub, k1;
+    double gth[8];
+    R adj_red[REED_MAX_WARPS][12];
     int Aold[3];
     int shift, rebuild, event, status, src, top, nclone;
     int need_count, active_count, n_out, out_ovf;
@@ -89,9 +95,10 @@ template <typename R, int TT> struct Layout {
     {
         return TT == REED_TT_TERSOFF ? align(sizeof(V2<R>) * cap * REED_MAXNB) : 0;
     }
-    static __host__ __device__ size_t total(int na, int cap)
+    static __host__ __device__ size_t adj_bytes(int na, int adj) { return adj ? 2 * align(sizeof(V4<R>) * na) : 0; }
+    static __host__ __device__ size_t total(int na, int cap, int adj = 0)
     {
-        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap) + bond_bytes(cap);
+        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap) + bond_bytes(cap) + adj_bytes(na, adj);
     }
     // bytes of one clone record: ion header + pos, vel, frc
     static __host__ __device__ size_t entry_bytes(int na) { return align(sizeof(IonState<R>)) + atoms_bytes(na); }
@@ -112,7 +119,9 @@ template <typename R, int TT> struct Win {
     uint16_t* nbr;        // neighbour atoms per slot
     uint16_t* outl;       // outlier atoms
     V2<R>* bond;          // per slot and neighbour: {1/2 dV/db db/dzeta, dV/dr}
-    __device__ Win(unsigned char* base, int na, int cap)
+    V4<R>* xbar;          // adjoint of positions (adjoint runs)
+    V4<R>* vbar;          // adjoint of velocities
+    __device__ Win(unsigned char* base, int na, int cap, int adj = 0)
     {
         using L = Layout<R, TT>;
         S = reinterpret_cast<TrackShared<R>*>(base);
@@ -143,7 +152,15 @@ template <typename R, int TT> struct Win {
             outl = reinterpret_cast<uint16_t*>(base + o);
             o += L::align(sizeof(uint16_t) * REED_OUTCAP);
         }
-        if constexpr (TT == REED_TT_TERSOFF) bond = reinterpret_cast<V2<R>*>(base + o);
+        if constexpr (TT == REED_TT_TERSOFF) {
+            bond = reinterpret_cast<V2<R>*>(base + o);
+            o += L::bond_bytes(cap);
+        }
+        xbar = vbar = nullptr;
+        if (adj) {
+            xbar = reinterpret_cast<V4<R>*>(base + o);
+            vbar = reinterpret_cast<V4<R>*>(base + o + L::align(sizeof(V4<R>) * na));
+        }
     }
 };
 
@@ -755,8 +772,10 @@ __device__ __forceinline__ void gather_partials(Win<R, TT>& W, R out[8])
 
 // Depth bin tally and per-track record of a finished track (Sec. 3: result
 // messages become atomics on device tallies).
-template <typename R> __device__ void finish_track(const DevParams& P, const DevBuf& B, const IonState<R>& I, int status)
+template <typename R>
+__device__ long long finish_track(const DevParams& P, const DevBuf& B, const IonState<R>& I, int status)
 {
+    long long kept = -1;
     const double w = ldexp(1.0, -I.level);
     if (status >= REED_TRACK_STOPPED && status <= REED_TRACK_TRUNCATED)
         atomicAdd(&B.counters[C_STOP + status - REED_TRACK_STOPPED], 1ull);
@@ -791,8 +810,10 @@ template <typename R> __device__ void finish_track(const DevParams& P, const Dev
             r.level = I.level;
             r.status = status;
             B.records[k] = r;
+            kept = (long long)k;
         }
     }
+    return kept;
 }
 
 // Launch a primary (Sec. 2; lateral position uniform in the (0,0) surface
@@ -862,6 +883,7 @@ template <typename R> __device__ void ion_prologue(const DevParams& P, const Hot
     R dt = H.dt_max;
     if (vmax * dt > H.dx_max) dt = H.dx_max / vmax;
     const R kd = drag_k<R>(H, S);
+    S->on1 = S->rel[2] >= S->zsurf;
     const R h = R(0.5) * dt * H.invM1;
     R de = R(0);
     for (int d = 0; d < 3; ++d) {
@@ -900,6 +922,7 @@ __device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShar
     I.rho = red[3];
     I.vmax2 = red[4];
     const R kd = drag_k<R>(H, S);
+    S->on2 = S->rel[2] >= S->zsurf;
     const R h = R(0.5) * dt * H.invM1;
     R de = R(0);
     for (int d = 0; d < 3; ++d) {
@@ -980,6 +1003,8 @@ __device__ void initial_forces(const DevParams& P, const HotParams<R>& H, Win<R,
     __syncthreads();
 }
 
+#include "reed_adjoint.cuh"
+
 // ---------------------------------------------------------------------------
 // The persistent kernel.
 // ---------------------------------------------------------------------------
@@ -988,10 +1013,11 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                                                          const __grid_constant__ DevBuf B)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    Win<R, TT> W(smem, P.na, P.bond_cap);
+    Win<R, TT> W(smem, P.na, P.bond_cap, P.adjoint);
     TrackShared<R>* S = W.S;
     const HotParams<R>& H = hot<R>(P);
     const int tid = threadIdx.x;
+    unsigned char* adjbase = (P.adjoint && B.adj) ? B.adj + (size_t)blockIdx.x * B.adj_stride : nullptr;
     unsigned char* stack = B.stacks ? B.stacks + (size_t)blockIdx.x * B.stack_stride : nullptr;
 
     // thread-0 counters, flushed at exit
@@ -1050,6 +1076,12 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             }
             __syncthreads();
             initial_forces<R, TT>(P, H, W, c_bonds, c_rebuild, nbovf, capovf, wc);
+            if constexpr (TT == REED_TT_NONE) {
+                if (adjbase) {   // checkpoint of the state before step 0
+                    save_state<R, TT>(P, W, adjbase);
+                    __syncthreads();
+                }
+            }
         } else {
             unsigned char* rec = stack + (size_t)(S->top - 1) * B.entry_bytes;
             if (tid == 0) {
@@ -1152,6 +1184,18 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                     int* a3 = B.trace_anchor + 3 * o;
                     a3[0] = I.A[0]; a3[1] = I.A[1]; a3[2] = I.A[2];
                 }
+                if (adjbase) {
+                    // frozen quantities of this step; checkpoints every adj_every steps
+                    StepRec<R>* ring = reinterpret_cast<StepRec<R>*>(adjbase + (size_t)P.adj_nck * B.entry_bytes);
+                    StepRec<R> sr;
+                    sr.dt = S->dt;
+                    sr.A[0] = S->ion.A[0];
+                    sr.A[1] = S->ion.A[1];
+                    sr.A[2] = S->ion.A[2];
+                    sr.flags = (S->on1 ? 1 : 0) | (S->on2 ? 2 : 0) | (shift ? 4 : 0);
+                    ring[(S->ion.steps - 1) % REED_STEP_RING] = sr;
+                    if (ev == EV_NONE && S->ion.steps % P.adj_every == 0) ev = EV_CKPT;
+                }
                 S->event = ev;
                 if (ev == EV_NONE) ion_prologue<R>(P, H, S);
             }
@@ -1164,6 +1208,13 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             }
             need_prologue = true;
             if (ev == EV_END) break;
+            if (ev == EV_CKPT) {
+                if constexpr (TT == REED_TT_NONE) {
+                    save_state<R, TT>(P, W, adjbase + (size_t)((S->ion.steps / P.adj_every) % P.adj_nck) * B.entry_bytes);
+                    __syncthreads();
+                }
+                continue;
+            }
             // ---- cloning (Sec. 2): push one record per level passed
             const int nc = S->nclone;
             __syncthreads();
@@ -1211,10 +1262,23 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                 ++c_fail;
                 atomicOr(B.status, ERR_NONFINITE);
             }
-            finish_track<R>(P, B, S->ion, S->status);
+            S->rec_index = finish_track<R>(P, B, S->ion, S->status);
             ++c_tracks;
         }
         __syncthreads();
+        if constexpr (TT == REED_TT_NONE) {
+            // truncated-segment sensitivities of the final depth
+            if (adjbase && B.grads && S->rec_index >= 0) {
+                double g[REED_NTHETA] = {0, 0, 0, 0, 0, 0, 0, 0};
+                if (S->status == REED_TRACK_STOPPED) {
+                    AdjScratch<R, TT> A(adjbase, P, B.entry_bytes);
+                    adjoint_track<R, TT>(P, H, W, A, g);
+                }
+                if (tid == 0)
+                    for (int k = 0; k < REED_NTHETA; ++k) B.grads[(size_t)S->rec_index * REED_NTHETA + k] = g[k];
+                __syncthreads();
+            }
+        }
     }
     if (nbovf || capovf) atomicOr(B.status, ERR_NEIGHBOR);
     // flush counters

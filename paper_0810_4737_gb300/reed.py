@@ -52,7 +52,8 @@ class reed_run_opts(C.Structure):
                 ("stream", C.c_void_p), ("adaptive", C.c_int32), ("reserved2", C.c_int32),
                 ("epoch_size", C.c_int64), ("n_initial", C.c_int64), ("target_tracks", C.c_int64),
                 ("damage_n", C.c_int32), ("reserved3", C.c_int32), ("damage_voxel", C.c_double),
-                ("damage_min", C.c_double)]
+                ("damage_min", C.c_double), ("adjoint", C.c_int32), ("adj_segment", C.c_int32),
+                ("adj_every", C.c_int32), ("reserved4", C.c_int32)]
 
 
 class reed_track_record(C.Structure):
@@ -81,7 +82,8 @@ class reed_stats_t(C.Structure):
 
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",
             "reed_reset", "reed_last_error", "reed_destroy", "reed_philox", "reed_cell_atoms", "reed_forces",
-            "reed_window_replay", "reed_run_static", "reed_thresholds", "reed_damage_map"]
+            "reed_window_replay", "reed_run_static", "reed_thresholds", "reed_damage_map", "reed_track_grads",
+            "reed_kde_profile", "reed_grad", "reed_set_theta"]
 
 _LIB = None
 _D = C.POINTER(C.c_double)
@@ -119,6 +121,10 @@ def lib():
         L.reed_reset.argtypes = [vp]
         L.reed_thresholds.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int)]
         L.reed_damage_map.argtypes = [vp, vp, C.c_int, vp]
+        L.reed_track_grads.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_int64)]
+        L.reed_kde_profile.argtypes = [vp, C.c_double, C.c_int, C.c_double, vp]
+        L.reed_grad.argtypes = [vp, C.c_double, C.c_int, C.c_double, vp, vp]
+        L.reed_set_theta.argtypes = [vp, _D]
         L.reed_last_error.argtypes = [vp]
         L.reed_last_error.restype = C.c_char_p
         L.reed_destroy.argtypes = [vp]
@@ -177,7 +183,7 @@ def potentials_struct(w) -> reed_potentials:
 
 def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, record=True, record_capacity=0,
              trace_tracks=0, trace_steps=0, stream=None, adaptive=False, epoch_size=4096, n_initial=50,
-             target_tracks=0, damage=True) -> reed_run_opts:
+             target_tracks=0, damage=True, adjoint=False, adj_segment=200, adj_every=20) -> reed_run_opts:
     o = reed_run_opts()
     o.dt_max_fs, o.dx_max, o.e_stop = w["dt_max_fs"], w["dx_max"], w["e_stop"]
     o.step_cap = int(w["step_cap"])
@@ -198,6 +204,7 @@ def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, reco
     o.epoch_size, o.n_initial, o.target_tracks = epoch_size, n_initial, target_tracks
     o.damage_n = int(w.get("damage_n", 0)) if damage else 0
     o.damage_voxel, o.damage_min = float(w.get("damage_voxel", 10.0)), float(w.get("damage_min", 0.1))
+    o.adjoint, o.adj_segment, o.adj_every = (1 if adjoint else 0), adj_segment, adj_every
     return o
 
 
@@ -260,6 +267,39 @@ def reed_damage_map(ctx, n):
     ov = np.zeros(1)
     _check(lib().reed_damage_map(ctx, out.ctypes.data, n, ov.ctypes.data), ctx)
     return out, float(ov[0])
+
+
+def reed_track_grads(ctx):
+    """(n_records, 8) per-track dz/dtheta of adjoint runs."""
+    n = C.c_int64(0)
+    _check(lib().reed_track_grads(ctx, None, 0, C.byref(n)), ctx)
+    out = np.zeros((n.value, 8))
+    if n.value:
+        _check(lib().reed_track_grads(ctx, out.ctypes.data, n.value, C.byref(n)), ctx)
+    return out
+
+
+def reed_kde_profile(ctx, sigma, n_bins, bin_width, out=None):
+    """Kernel-density range profile (A^-1); out may be a device pointer."""
+    if out is None:
+        p = np.zeros(n_bins)
+        _check(lib().reed_kde_profile(ctx, sigma, n_bins, bin_width, p.ctypes.data), ctx)
+        return p
+    _check(lib().reed_kde_profile(ctx, sigma, n_bins, bin_width, out), ctx)
+    return None
+
+
+def reed_grad(ctx, sigma, n_bins, bin_width, dL_dp_ptr):
+    """dL/dtheta (8) for a profile cotangent at dL_dp_ptr (host or device)."""
+    g = np.zeros(8)
+    _check(lib().reed_grad(ctx, sigma, n_bins, bin_width, dL_dp_ptr, g.ctypes.data), ctx)
+    return g
+
+
+def reed_set_theta(ctx, theta):
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    assert t.size == 8
+    _check(lib().reed_set_theta(ctx, t.ctypes.data_as(_D)), ctx)
 
 
 def reed_reset(ctx):
@@ -371,6 +411,12 @@ class Reed:
     def damage_map(self):
         return reed_damage_map(self.ctx, int(self.w["damage_n"]))
 
+    def track_grads(self):
+        return reed_track_grads(self.ctx)
+
+    def set_theta(self, theta):
+        reed_set_theta(self.ctx, theta)
+
     def forces(self, ion_x, xyz, sp, precision=PREC_MIXED):
         ion = self.w["ion"]
         return reed_forces(self.ctx, precision, ion["Z"], ion["M"], ion_x, xyz, sp)
@@ -397,3 +443,40 @@ class Reed:
             self.close()
         except Exception:
             pass
+
+
+class ProfileFunction:
+    """Differentiable kernel-density range profile, p(theta), theta = (s_e,
+    s_loc, c_1..c_6) as a torch.autograd.Function: forward runs the tracks
+    with the truncated-segment adjoint on and returns the profile (a float64
+    CUDA tensor of n_bins); backward returns dL/dtheta from the per-track
+    sensitivities (include/reed.h: reed_grad)."""
+
+    @staticmethod
+    def make(w, n_ions, seed, sigma, n_bins, bin_width, precision=PREC_MIXED):
+        import torch
+
+        ctx_holder = {}
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, theta):
+                if "r" not in ctx_holder:
+                    ctx_holder["r"] = Reed(w)
+                r = ctx_holder["r"]
+                r.reset()
+                r.set_theta(theta.detach().double().cpu().numpy())
+                stream = torch.cuda.current_stream().cuda_stream or None
+                r.run(n_ions=n_ions, seed=seed, precision=precision, adjoint=True, stream=stream)
+                p = torch.empty(n_bins, dtype=torch.float64, device="cuda")
+                reed_kde_profile(r.ctx, sigma, n_bins, bin_width, p.data_ptr())
+                return p
+
+            @staticmethod
+            def backward(fctx, gp):
+                r = ctx_holder["r"]
+                gp = gp.detach().double().contiguous()
+                g = reed_grad(r.ctx, sigma, n_bins, bin_width, gp.data_ptr())
+                return torch.as_tensor(g, dtype=torch.float64, device=gp.device)
+
+        return _Fn.apply, ctx_holder

@@ -464,6 +464,7 @@ class ProfileFunction:
                 if "r" not in ctx_holder:
                     ctx_holder["r"] = Reed(w)
                 r = ctx_holder["r"]
+                fctx.theta_device = theta.device
                 r.reset()
                 r.set_theta(theta.detach().double().cpu().numpy())
                 stream = torch.cuda.current_stream().cuda_stream or None
@@ -477,6 +478,6 @@ class ProfileFunction:
                 r = ctx_holder["r"]
                 gp = gp.detach().double().contiguous()
                 g = reed_grad(r.ctx, sigma, n_bins, bin_width, gp.data_ptr())
-                return torch.as_tensor(g, dtype=torch.float64, device=gp.device)
+                return torch.as_tensor(g, dtype=torch.float64, device=fctx.theta_device)
 
         return _Fn.apply, ctx_holder

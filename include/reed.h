@@ -168,6 +168,10 @@ typedef struct {
     int32_t adj_segment;
     int32_t adj_every;
     int32_t reserved4;
+    /* Target neighbour lists (Tersoff, Buckingham): list radius = cutoff +
+     * nl_skin; a list is rebuilt after a window move and when the two longest
+     * atom paths since the last build add up to more than nl_skin.  0 = 0.3 A. */
+    double nl_skin;
 } reed_run_opts;
 
 /* Per-track result: the depth and weight of one finished track (Sec. 3, result messages). */

@@ -37,7 +37,7 @@ const double kFluorite[12][3] = {{0, 0, 0},       {0, .5, .5},     {.5, 0, .5}, 
 // ZBL-correction knot radii (A); B-splines are centred on ln r of each.
 const double kKnots[6] = {0.2, 0.35, 0.6, 1.0, 1.7, 3.0};
 
-const double kSkin = 0.3;   // neighbour-list skin, A
+const double kSkin = 0.3;   // default neighbour-list skin, A
 #define REED_NTHETA_HOST 8
 #define REED_STEP_RING_HOST 256
 
@@ -165,7 +165,7 @@ template <typename T> void fill_hot(HotParams<T>& h, const DevParams& P, const r
     h.t_zia = (T)screen_inv(P.Z2[0], P.Z2[0]);
     double cut = P.tt == REED_TT_BUCKINGHAM ? q.buck_cut[1] : R + D;
     h.rlist2 = (T)((cut + skin) * (cut + skin));
-    h.skin_half = (T)(0.5 * skin);
+    h.skin = (T)skin;
     // Buckingham
     for (int p = 0; p < 3; ++p) {
         h.bA[p] = (T)q.buck_A[p];
@@ -224,7 +224,7 @@ double lindhard_gamma_unit(const reed_ctx* ctx, double Z1, double M1)
 // Rows of Tersoff bond storage: atoms of a perfect bulk window that are
 // integrated or within the list radius of an integrated atom, plus 25 %
 // head-room for disorder and cascades (capped at the window size).
-int bond_capacity(const DevParams& P)
+int bond_capacity(const DevParams& P, double skin)
 {
     if (P.tt == REED_TT_NONE) return 0;
     if (P.margin == 0) return P.na;
@@ -232,7 +232,7 @@ int bond_capacity(const DevParams& P)
         const int k = P.n - 2 * P.margin;
         return k * k * k * P.nb;
     }
-    const double rl = P.hd.tcut + kSkin;
+    const double rl = P.hd.tcut + skin;
     std::vector<double> x;
     std::vector<char> act;
     for (int i = 0; i < P.n; ++i)
@@ -330,9 +330,12 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.dvox = o.damage_voxel > 0 ? o.damage_voxel : 10.0;
     P.dhalf = 0.5 * P.dn * P.dvox;
     P.dmin = o.damage_min;
-    fill_hot<float>(P.hf, P, ctx, kSkin);
-    fill_hot<double>(P.hd, P, ctx, kSkin);
-    P.bond_cap = bond_capacity(P);
+    const double skin = o.nl_skin > 0.0 ? o.nl_skin : kSkin;
+    fill_hot<float>(P.hf, P, ctx, skin);
+    fill_hot<double>(P.hd, P, ctx, skin);
+    P.bond_cap = bond_capacity(P, skin);
+    // the home-cell candidate search needs a - 2 REED_DISPLACED > list radius
+    P.nl_brute = !(P.a - 2.0 * REED_DISPLACED > P.hd.tcut + skin) ? 1 : 0;
     return REED_OK;
 }
 
@@ -626,6 +629,7 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
             return fail(ctx, REED_E_ARG, "adj_segment must be a multiple of adj_every and adj_segment + adj_every <= %d",
                         REED_STEP_RING_HOST);
         P.adjoint = 1;
+        P.rho_on = 1;   // d/ds_loc needs the local density even at s_loc = 0
         P.adj_seg = seg;
         P.adj_every = every;
         P.adj_nck = seg / every + 1;

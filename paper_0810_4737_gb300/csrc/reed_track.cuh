@@ -67,6 +67,7 @@ template <typename R> struct TrackShared {
     int scan[2][REED_MAX_WARPS];
     long long pidx;
     R red[REED_MAX_WARPS][8];
+    R path2[REED_MAX_WARPS][2];   // per warp: the two longest atom paths since the list build
 };
 
 template <typename R> struct V2 { R a, b; };
@@ -277,16 +278,17 @@ template <typename R> __device__ __forceinline__ int species_of(const V4<R>& p) 
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Target neighbour lists.  Rebuilt at track start, after a window move and
-// when some atom has travelled more than half the skin since the last build.
+// when the two longest atom paths since the last build add up to more than
+// the skin (a pair can then have closed in from beyond the list radius).
 // Candidates of an atom are the atoms of the 27 home cells around its own
 // (the ring layout stores each cell's atoms contiguously) plus the
 // "outliers": atoms more than REED_DISPLACED from their home-cell box, which
 // are checked against everyone.  Two non-outliers closer than rlist always
-// sit in neighbouring home cells because a - 2 REED_DISPLACED > rlist.
+// sit in neighbouring home cells when a - 2 REED_DISPLACED > rlist (else
+// every list is searched by brute force).
 // Integrated atoms get list slots first; atoms bonded to them next.
 // Called by all threads right after a barrier; ends with a barrier.
 // ---------------------------------------------------------------------------
-#define REED_DISPLACED 1.0
 
 template <typename R, int TT>
 __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int i, int slot,
@@ -426,7 +428,7 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
     }
     __syncthreads();
     // pair lists reach further than a - 2 REED_DISPLACED: search every atom
-    const bool brute = force_brute || S->out_ovf != 0 || TT == REED_TT_BUCKINGHAM;
+    const bool brute = force_brute || S->out_ovf != 0 || P.nl_brute || TT == REED_TT_BUCKINGHAM;
     // lists of integrated atoms; their other neighbours become pending
     for (int k = threadIdx.x; k < nact_slots; k += blockDim.x) {
         const int i = W.slot_atom[k];
@@ -1114,6 +1116,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             const uint64_t key = S->ion.key;
             // phase A: re-anchor and first half kick + drift of own atoms
             bool any_new = false;
+            R pm1 = R(0), pm2 = R(0);   // this thread's two longest paths
             for (int i = tid; i < P.na; i += blockDim.x) {
                 V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
                 if (shift) {
@@ -1135,7 +1138,12 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
                     p.z += sz;
                     if constexpr (TT != REED_TT_NONE) {
                         { const R l2 = sx * sx + sy * sy + sz * sz; if (l2 > R(0)) v.w += l2 * Mth<R>::rsqrt(l2); }
-                        if (v.w > H.skin_half) S->rebuild = 1;
+                        if (v.w > pm1) {
+                            pm2 = pm1;
+                            pm1 = v.w;
+                        } else if (v.w > pm2) {
+                            pm2 = v.w;
+                        }
                     }
                 }
                 W.pos[i] = p;
@@ -1144,16 +1152,29 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             }
             (void)any_new;
             if constexpr (TT != REED_TT_NONE) {
-                if (tid == 0 && shift) S->rebuild = 1;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const R q1 = __shfl_xor_sync(0xffffffffu, pm1, o), q2 = __shfl_xor_sync(0xffffffffu, pm2, o);
+                    pm2 = fmax(fmin(pm1, q1), fmax(pm2, q2));
+                    pm1 = fmax(pm1, q1);
+                }
+                if ((tid & 31) == 0) {
+                    S->path2[tid >> 5][0] = pm1;
+                    S->path2[tid >> 5][1] = pm2;
+                }
                 __syncthreads();
                 lap(PH_MOVE);
-                if (S->rebuild) {
+                // every thread merges the per-warp pairs in the same order
+                R m1 = R(0), m2 = R(0);
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    const R q1 = S->path2[w][0], q2 = S->path2[w][1];
+                    m2 = fmax(fmin(m1, q1), fmax(m2, q2));
+                    m1 = fmax(m1, q1);
+                }
+                if (shift || m1 + m2 > H.skin) {
                     build_neighbours<R, TT>(P, H, W, nbovf, capovf);
                     __syncthreads();
-                    if (tid == 0) {
-                        S->rebuild = 0;
-                        ++c_rebuild;
-                    }
+                    if (tid == 0) ++c_rebuild;
                     lap(PH_BUILD);
                 }
                 if constexpr (TT == REED_TT_TERSOFF) {

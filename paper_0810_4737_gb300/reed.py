@@ -53,7 +53,8 @@ class reed_run_opts(C.Structure):
                 ("epoch_size", C.c_int64), ("n_initial", C.c_int64), ("target_tracks", C.c_int64),
                 ("damage_n", C.c_int32), ("reserved3", C.c_int32), ("damage_voxel", C.c_double),
                 ("damage_min", C.c_double), ("adjoint", C.c_int32), ("adj_segment", C.c_int32),
-                ("adj_every", C.c_int32), ("reserved4", C.c_int32)]
+                ("adj_every", C.c_int32), ("reserved4", C.c_int32),
+                ("nl_skin", C.c_double)]
 
 
 class reed_track_record(C.Structure):
@@ -183,7 +184,7 @@ def potentials_struct(w) -> reed_potentials:
 
 def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, record=True, record_capacity=0,
              trace_tracks=0, trace_steps=0, stream=None, adaptive=False, epoch_size=4096, n_initial=50,
-             target_tracks=0, damage=True, adjoint=False, adj_segment=200, adj_every=20) -> reed_run_opts:
+             target_tracks=0, damage=True, adjoint=False, adj_segment=200, adj_every=20, nl_skin=0.0) -> reed_run_opts:
     o = reed_run_opts()
     o.dt_max_fs, o.dx_max, o.e_stop = w["dt_max_fs"], w["dx_max"], w["e_stop"]
     o.step_cap = int(w["step_cap"])
@@ -205,6 +206,7 @@ def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, reco
     o.damage_n = int(w.get("damage_n", 0)) if damage else 0
     o.damage_voxel, o.damage_min = float(w.get("damage_voxel", 10.0)), float(w.get("damage_min", 0.1))
     o.adjoint, o.adj_segment, o.adj_every = (1 if adjoint else 0), adj_segment, adj_every
+    o.nl_skin = nl_skin
     return o
 
 

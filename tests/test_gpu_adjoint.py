@@ -1,17 +1,18 @@
 """GPU parity of the truncated-segment sensitivities (the adjoint workload).
 
 * per-track dz_T/dtheta from the GPU's reverse pass agrees with the oracle's
-  forward-mode tangents through the same frozen segment, on every track
-  whose GPU trajectory coincides with the oracle's (same stop step, same
-  depth); trajectories are chaotic, so the test also asks that most tracks
-  coincide in the plain FP64 form;
-* theta away from its default (s_loc and spline coefficients non-zero);
+  forward-mode tangents through the same frozen segment on short tracks
+  (where the two trajectories coincide), for segments that start at the
+  launch state and at a checkpoint, at the default theta and away from it;
+* on full tracks (chaotic, so trajectories part) the per-track
+  sensitivities of GPU and oracle have the same means;
 * the kernel-density profile and the gradient contraction agree with numpy
   on the GPU's own records and per-track sensitivities;
 * the autograd wrapper's backward equals the C-ABI contraction;
 * at the full workload size (16384 B ions, 10 keV, 300 K) every stopped
   track carries finite sensitivities, reproducible track by track.
 """
+import os
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
@@ -31,60 +32,78 @@ def R():
     return reed
 
 
-def _oracle_tangents(O, p, seed, ids):
+def _oracle_tangents(O, p, seed, ids, seg=200, every=20):
     def one(t):
         try:
-            return O.segment_tangent(p, seed, int(t))
+            return O.segment_tangent(p, seed, int(t), seg, every)
         except ValueError:
             return None
-    with ThreadPoolExecutor(max_workers=8) as ex:
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
         return list(ex.map(one, ids))
 
 
-def _compare(R, O, w, n, prec, ztol, gtol, seed=0):
-    p = O.params(w)
+def _gpu(R, w, n, prec, seed=0, **kw):
     with R.Reed(w) as ctx:
-        ctx.run(n_ions=n, seed=seed, precision=prec, record=True, adjoint=True)
+        ctx.run(n_ions=n, seed=seed, precision=prec, record=True, adjoint=True, **kw)
         rec = ctx.records()
         g = ctx.track_grads()
     assert len(rec) == n and g.shape == (n, 8)
+    # tracks that are not stopped carry no sensitivity
+    assert np.all(g[rec["status"] != STOPPED] == 0.0)
+    assert np.all(np.isfinite(g))
+    return rec, g
+
+
+THETA = {"default": {}, "shifted": dict(s_loc=0.1, spline_c=[0.02, -0.01, 0.03, 0.0, 0.01, -0.02])}
+
+
+@pytest.mark.parametrize("theta", ["default", "shifted"])
+@pytest.mark.parametrize("seg,every", [(220, 20), (100, 20), (60, 10)])
+@pytest.mark.parametrize("prec", [1, 0])
+def test_short_track_sensitivities_match_oracle(R, O, prec, seg, every, theta):
+    # 1 keV B stopped at 900 eV: tracks of ~100-300 steps, short enough for
+    # the GPU and oracle trajectories to coincide, so every segment (from the
+    # launch state when T <= seg, else from a checkpoint) is compared
+    w = workload("b10kev_si_300k_adjoint", energy=1000.0, e_stop=900.0, **THETA[theta])
+    n = 24
+    rec, g = _gpu(R, w, n, prec, adj_segment=seg, adj_every=every)
+    p = O.params(w)
     stopped = np.nonzero(rec["status"] == STOPPED)[0]
-    refs = _oracle_tangents(O, p, seed, rec["primary"][stopped])
-    matched, worst = 0, 0.0
+    assert len(stopped) >= n // 2
+    refs = _oracle_tangents(O, p, 0, rec["primary"][stopped], seg, every)
+    ztol, gtol = (1e-7, 1e-6) if prec == 1 else (1e-3, 2e-2)
+    compared = 0
     for i, ref in zip(stopped, refs):
-        assert np.all(np.isfinite(g[i]))
-        if ref is None or ref["T"] != rec["steps"][i] or abs(ref["z"] - rec["z"][i]) > ztol:
-            continue
-        matched += 1
+        assert ref is not None
+        if prec == 0 and (ref["T"] != rec["steps"][i] or abs(ref["z"] - rec["z"][i]) > ztol):
+            continue   # FP32 forces: an occasional trajectory parts from the FP64 one
+        assert ref["T"] == rec["steps"][i] and abs(ref["z"] - rec["z"][i]) <= ztol, (i, ref, rec[i])
+        compared += 1
         scale = np.maximum(np.abs(ref["grad"]), 1e-3 * np.max(np.abs(ref["grad"])))
         err = np.max(np.abs(g[i] - ref["grad"]) / scale)
-        worst = max(worst, err)
-        assert err <= gtol, (i, g[i], ref["grad"])
-    # tracks that are not stopped carry no sensitivity
-    others = np.nonzero(rec["status"] != STOPPED)[0]
-    assert np.all(g[others] == 0.0)
-    return matched, len(stopped), worst
+        assert err <= gtol, (i, g[i], ref["grad"], err)
+    assert compared >= (len(stopped) if prec == 1 else 3 * len(stopped) // 4)
 
 
-@pytest.mark.parametrize("prec", [1, 0])
-def test_track_sensitivities_match_oracle_tangents(R, O, prec):
-    w = workload("b10kev_si_300k_adjoint", energy=600.0, sigma=0.0)
-    if prec == 1:
-        matched, total, worst = _compare(R, O, w, 24, prec, 1e-6, 1e-5)
-        assert matched >= total // 2, (matched, total)
-    else:
-        # FP32 forces: the trajectory drifts by ~1e-4 A over a few hundred
-        # steps, so fewer tracks coincide and the sensitivities agree to the
-        # FP32 level only
-        matched, total, worst = _compare(R, O, w, 24, prec, 2e-3, 5e-2)
-        assert matched >= 1, (matched, total)
-
-
-def test_track_sensitivities_nondefault_theta(R, O):
-    w = workload("b10kev_si_300k_adjoint", energy=2000.0, sigma=0.0, s_loc=0.2,
-                 spline_c=[0.02, -0.01, 0.03, 0.0, 0.01, -0.02])
-    matched, total, worst = _compare(R, O, w, 16, 1, 1e-6, 1e-5)
-    assert matched >= total // 2, (matched, total)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_long_track_sensitivities_statistics(R, O, prec):
+    # 2 keV B, full tracks: trajectories part after a few hundred steps, so
+    # the GPU's and the oracle's per-track sensitivities are compared as two
+    # samples of the same distribution (per-parameter means, Welch t)
+    w = workload("b10kev_si_300k_adjoint", energy=2000.0, **THETA["shifted"])
+    n = 384
+    rec, g = _gpu(R, w, n, prec)
+    s = rec["status"] == STOPPED
+    refs = [r for r in _oracle_tangents(O, O.params(w), 0, np.arange(n)) if r is not None]
+    a = g[s]
+    b = np.array([r["grad"] for r in refs])
+    for k in range(8):
+        va, vb = a[:, k].var(ddof=1) / len(a), b[:, k].var(ddof=1) / len(b)
+        if va + vb == 0.0:
+            assert a[:, k].mean() == b[:, k].mean() == 0.0
+            continue
+        t = (a[:, k].mean() - b[:, k].mean()) / np.sqrt(va + vb)
+        assert abs(t) < 4.5, (k, a[:, k].mean(), b[:, k].mean(), t)
 
 
 def _np_profile(rec, sigma, nb, bw):

@@ -166,6 +166,8 @@ template <typename T> void fill_hot(HotParams<T>& h, const DevParams& P, const r
     double cut = P.tt == REED_TT_BUCKINGHAM ? q.buck_cut[1] : R + D;
     h.rlist2 = (T)((cut + skin) * (cut + skin));
     h.skin = (T)skin;
+    h.g_lo = (T)(-P.half_n * P.a);
+    h.g_inv = (T)(P.g_nb / (P.n * P.a));
     // Buckingham
     for (int p = 0; p < 3; ++p) {
         h.bA[p] = (T)q.buck_A[p];
@@ -331,11 +333,17 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.dhalf = 0.5 * P.dn * P.dvox;
     P.dmin = o.damage_min;
     const double skin = o.nl_skin > 0.0 ? o.nl_skin : kSkin;
+    // neighbour-search grid over the window: bins no narrower than the list
+    // radius (with a margin for rounding), at most 10 per axis
+    {
+        const double rl = (P.tt == REED_TT_BUCKINGHAM ? ctx->pot.buck_cut[1]
+                                                     : ctx->pot.tersoff[9] + ctx->pot.tersoff[10]) + skin;
+        P.g_nb = std::max(1, std::min(10, (int)std::floor(P.n * P.a / (rl * 1.001))));
+        P.g_nbins = P.g_nb * P.g_nb * P.g_nb;
+    }
     fill_hot<float>(P.hf, P, ctx, skin);
     fill_hot<double>(P.hd, P, ctx, skin);
     P.bond_cap = bond_capacity(P, skin);
-    // the home-cell candidate search needs a - 2 REED_DISPLACED > list radius
-    P.nl_brute = !(P.a - 2.0 * REED_DISPLACED > P.hd.tcut + skin) ? 1 : 0;
     return REED_OK;
 }
 
@@ -634,8 +642,8 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
         P.adj_every = every;
         P.adj_nck = seg / every + 1;
     }
-    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap, P.adjoint)
-                            : reed_f32::smem_bytes(tt, P.na, P.bond_cap, P.adjoint);
+    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap, P.adjoint, P.g_nbins)
+                            : reed_f32::smem_bytes(tt, P.na, P.bond_cap, P.adjoint, P.g_nbins);
     if (smem > ctx->smem_optin)
         return fail(ctx, REED_E_SMEM, "window of %d atoms needs %zu B of shared memory (max %zu)", P.na, smem,
                     ctx->smem_optin);
@@ -643,7 +651,8 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     L.threads = o.threads_per_track ? o.threads_per_track : (tt == REED_TT_NONE ? 64 : 256);
     L.smem = smem;
     int occ = 0;
-    CK(f64 ? reed_f64::occupancy(tt, L.threads, smem, &occ) : reed_f32::occupancy(tt, L.threads, smem, &occ));
+    CK(f64 ? reed_f64::occupancy(tt, L.threads, smem, &occ, P.adjoint)
+           : reed_f32::occupancy(tt, L.threads, smem, &occ, P.adjoint));
     if (occ < 1) return fail(ctx, REED_E_SMEM, "kernel does not fit on an SM (%zu B shared, %d threads)", smem, L.threads);
     L.ctas_per_sm = o.ctas_per_sm ? std::min(o.ctas_per_sm, occ) : occ;
     L.grid = ctx->sms * L.ctas_per_sm;
@@ -1096,7 +1105,8 @@ int reed_forces(reed_ctx* ctx, int precision, double ion_Z, double ion_M, const 
         if (sp[i] < 0 || sp[i] >= ctx->nspec) return fail(ctx, REED_E_ARG, "species %d out of range", sp[i]);
     const bool f64 = precision == REED_PREC_FP64;
     if (P.tt == REED_TT_TERSOFF) P.bond_cap = std::max(n, 1);   // every given atom is integrated
-    size_t smem = f64 ? reed_f64::smem_bytes(P.tt, P.na, P.bond_cap) : reed_f32::smem_bytes(P.tt, P.na, P.bond_cap);
+    size_t smem = f64 ? reed_f64::smem_bytes(P.tt, P.na, P.bond_cap, 0, P.g_nbins)
+                      : reed_f32::smem_bytes(P.tt, P.na, P.bond_cap, 0, P.g_nbins);
     if (smem > ctx->smem_optin) return fail(ctx, REED_E_SMEM, "window needs %zu B shared memory", smem);
     size_t bx = up16(sizeof(double) * 3 * (size_t)std::max(n, 1)), bs = up16(sizeof(int) * (size_t)std::max(n, 1));
     size_t bi = up16(sizeof(double) * 3), bo = up16(sizeof(double) * (5 + 3 * (size_t)std::max(n, 1)));
@@ -1274,14 +1284,16 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
 
     const int tt = P.tt;
     const bool f64 = o.precision == REED_PREC_FP64;
-    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap) : reed_f32::smem_bytes(tt, P.na, P.bond_cap);
+    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap, 0, P.g_nbins)
+                            : reed_f32::smem_bytes(tt, P.na, P.bond_cap, 0, P.g_nbins);
     if (smem > (size_t)optin)
         return fail(nullptr, REED_E_SMEM, "window of %d atoms needs %zu B of shared memory (max %d)", P.na, smem, optin);
     LaunchCfg L;
     L.threads = o.threads_per_track ? o.threads_per_track : (tt == REED_TT_NONE ? 64 : 256);
     L.smem = smem;
     int occ = 0;
-    CK(f64 ? reed_f64::occupancy(tt, L.threads, smem, &occ) : reed_f32::occupancy(tt, L.threads, smem, &occ));
+    CK(f64 ? reed_f64::occupancy(tt, L.threads, smem, &occ, P.adjoint)
+           : reed_f32::occupancy(tt, L.threads, smem, &occ, P.adjoint));
     if (occ < 1) return fail(nullptr, REED_E_SMEM, "kernel does not fit on an SM");
     L.ctas_per_sm = o.ctas_per_sm ? std::min(o.ctas_per_sm, occ) : occ;
 

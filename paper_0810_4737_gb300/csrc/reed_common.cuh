@@ -51,6 +51,7 @@ template <typename R> struct HotParams {
     // Tersoff
     R tA, tB, tl1, tl2, tbn, tn, tmhn, tc2, td2, th, tRmD, tcut, tq, tdq, tR, tc2d2;
     R t_blo, t_binvw, t_zk, t_zia, rlist2, skin;
+    R g_lo, g_inv;   // neighbour-search grid: low corner (anchor frame) and bins per A
     // Buckingham
     R bA[3], brho_inv[3], bC[3], b_lo, b_binvw, b_rt, b_rinvw, b_rc2, b_zk[3], b_zia[3];
     // ion step
@@ -58,16 +59,12 @@ template <typename R> struct HotParams {
 };
 
 // Everything a launch needs, passed by value (__grid_constant__).
-// Atoms further than this (A) outside their home-cell box are neighbour-list
-// "outliers", searched against every atom.
-#define REED_DISPLACED 1.0
-
 struct DevParams {
     HotParams<float> hf;
     HotParams<double> hd;
     // lattice and window (Sec. 2 "Second")
     int kind, n, margin, nb, na, nspec, half_n;   // half_n = n / 2
-    int nl_brute;                                  // list radius too long for the home-cell search
+    int g_nb, g_nbins;                             // neighbour-search grid: bins per axis, in all
     double a, inv_a, sigma, anchor_shift;          // anchor_shift = 0.5 for even n
     double bas[REED_MAX_BASIS][3];
     int bspec[REED_MAX_BASIS];

@@ -63,7 +63,7 @@ template <typename R> struct TrackShared {
     R adj_red[REED_MAX_WARPS][12];
     int Aold[3];
     int shift, rebuild, event, status, src, top, nclone;
-    int need_count, active_count, n_out, out_ovf;
+    int need_count, active_count;
     int scan[2][REED_MAX_WARPS];
     long long pidx;
     R red[REED_MAX_WARPS][8];
@@ -75,31 +75,33 @@ template <typename R> struct V2 { R a, b; };
 // Shared-memory carve-up for a window of na atoms.  Target neighbour lists
 // and Tersoff bond data are kept only for "needed" atoms -- integrated atoms
 // (slots 0 .. active_count-1) and atoms bonded to them -- at most cap of
-// them, addressed through need_map (atom -> slot) and slot_atom.
-#define REED_OUTCAP 64
+// them, addressed through need_map (atom -> slot) and slot_atom.  The
+// neighbour search bins atoms on a grid of nbins cells (bin_count is all
+// zero between builds).
 
 template <typename R, int TT> struct Layout {
     static __host__ __device__ size_t align(size_t x) { return (x + 15) & ~(size_t)15; }
     static __host__ __device__ size_t shared_bytes() { return align(sizeof(TrackShared<R>)); }
     static __host__ __device__ size_t atoms_bytes(int na) { return 3 * align(sizeof(V4<R>) * na); }
-    static __host__ __device__ size_t nbr_bytes(int na, int cap)
+    static __host__ __device__ size_t nbr_bytes(int na, int cap, int nbins)
     {
         if (TT == REED_TT_NONE) return 0;
         return align(sizeof(uint16_t) * na) +            // need_map
-               align(na) +                               // flags
+               align(sizeof(uint16_t) * na) +            // binned (atoms in bin order)
+               align(sizeof(uint16_t) * (nbins + 1)) +   // bin_start
+               align(sizeof(unsigned) * nbins) +         // bin_count
                align(sizeof(uint16_t) * cap) +           // slot_atom
                align(cap) +                              // nnb
-               align(sizeof(uint16_t) * cap * maxnb(TT)) +    // nbr
-               align(sizeof(uint16_t) * REED_OUTCAP);    // outliers
+               align(sizeof(uint16_t) * cap * maxnb(TT));     // nbr
     }
     static __host__ __device__ size_t bond_bytes(int cap)
     {
         return TT == REED_TT_TERSOFF ? align(sizeof(V2<R>) * cap * REED_MAXNB) : 0;
     }
     static __host__ __device__ size_t adj_bytes(int na, int adj) { return adj ? 2 * align(sizeof(V4<R>) * na) : 0; }
-    static __host__ __device__ size_t total(int na, int cap, int adj = 0)
+    static __host__ __device__ size_t total(int na, int cap, int adj = 0, int nbins = 0)
     {
-        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap) + bond_bytes(cap) + adj_bytes(na, adj);
+        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap, nbins) + bond_bytes(cap) + adj_bytes(na, adj);
     }
     // bytes of one clone record: ion header + pos, vel, frc
     static __host__ __device__ size_t entry_bytes(int na) { return align(sizeof(IonState<R>)) + atoms_bytes(na); }
@@ -114,15 +116,22 @@ template <typename R, int TT> struct Win {
     V4<R>* vel;
     V4<R>* frc;
     uint16_t* need_map;   // atom -> list slot
-    uint8_t* flags;       // bit 0: outlier (far from its home cell)
+    uint16_t* binned;     // present atoms in bin order (atom order inside a bin)
+    uint16_t* bin_start;  // bin -> first entry in binned (nbins + 1)
+    unsigned* bin_count;  // scratch of the build, zero between builds
     uint16_t* slot_atom;  // list slot -> atom
     uint8_t* nnb;         // neighbours per slot
     uint16_t* nbr;        // neighbour atoms per slot
-    uint16_t* outl;       // outlier atoms
     V2<R>* bond;          // per slot and neighbour: {1/2 dV/db db/dzeta, dV/dr}
     V4<R>* xbar;          // adjoint of positions (adjoint runs)
     V4<R>* vbar;          // adjoint of velocities
-    __device__ Win(unsigned char* base, int na, int cap, int adj = 0)
+    // zero the bin counters (all threads; a barrier must follow)
+    __device__ void clear_grid(const DevParams& P)
+    {
+        if (bin_count)
+            for (int b = threadIdx.x; b < P.g_nbins; b += blockDim.x) bin_count[b] = 0u;
+    }
+    __device__ Win(unsigned char* base, int na, int cap, int adj = 0, int nbins = 0)
     {
         using L = Layout<R, TT>;
         S = reinterpret_cast<TrackShared<R>*>(base);
@@ -133,25 +142,28 @@ template <typename R, int TT> struct Win {
         frc = reinterpret_cast<V4<R>*>(base + o + 2 * ab);
         o += 3 * ab;
         need_map = nullptr;
-        flags = nullptr;
+        binned = nullptr;
+        bin_start = nullptr;
+        bin_count = nullptr;
         slot_atom = nullptr;
         nnb = nullptr;
         nbr = nullptr;
-        outl = nullptr;
         bond = nullptr;
         if constexpr (TT != REED_TT_NONE) {
             need_map = reinterpret_cast<uint16_t*>(base + o);
             o += L::align(sizeof(uint16_t) * na);
-            flags = base + o;
-            o += L::align(na);
+            binned = reinterpret_cast<uint16_t*>(base + o);
+            o += L::align(sizeof(uint16_t) * na);
+            bin_start = reinterpret_cast<uint16_t*>(base + o);
+            o += L::align(sizeof(uint16_t) * (nbins + 1));
+            bin_count = reinterpret_cast<unsigned*>(base + o);
+            o += L::align(sizeof(unsigned) * nbins);
             slot_atom = reinterpret_cast<uint16_t*>(base + o);
             o += L::align(sizeof(uint16_t) * cap);
             nnb = base + o;
             o += L::align(cap);
             nbr = reinterpret_cast<uint16_t*>(base + o);
             o += L::align(sizeof(uint16_t) * cap * maxnb(TT));
-            outl = reinterpret_cast<uint16_t*>(base + o);
-            o += L::align(sizeof(uint16_t) * REED_OUTCAP);
         }
         if constexpr (TT == REED_TT_TERSOFF) {
             bond = reinterpret_cast<V2<R>*>(base + o);
@@ -280,64 +292,64 @@ template <typename R> __device__ __forceinline__ int species_of(const V4<R>& p) 
 // Target neighbour lists.  Rebuilt at track start, after a window move and
 // when the two longest atom paths since the last build add up to more than
 // the skin (a pair can then have closed in from beyond the list radius).
-// Candidates of an atom are the atoms of the 27 home cells around its own
-// (the ring layout stores each cell's atoms contiguously) plus the
-// "outliers": atoms more than REED_DISPLACED from their home-cell box, which
-// are checked against everyone.  Two non-outliers closer than rlist always
-// sit in neighbouring home cells when a - 2 REED_DISPLACED > rlist (else
-// every list is searched by brute force).
+// Candidates come from a grid over the window whose bins are at least one
+// list radius wide: atoms closer than that sit in the same or adjacent bins.
+// Bin indices are clamped to the grid, which keeps that property for atoms
+// that have left the window's volume.  Inside a bin atoms are kept in atom
+// order, so lists do not depend on thread timing.
 // Integrated atoms get list slots first; atoms bonded to them next.
 // Called by all threads right after a barrier; ends with a barrier.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int floor_int(float x) { return __float2int_rd(x); }
+__device__ __forceinline__ int floor_int(double x) { return __double2int_rd(x); }
+
+template <typename R>
+__device__ __forceinline__ int grid_axis(const DevParams& P, const HotParams<R>& H, R x)
+{
+    return min(max(floor_int((x - H.g_lo) * H.g_inv), 0), P.g_nb - 1);
+}
+
+template <typename R>
+__device__ __forceinline__ int grid_bin(const DevParams& P, const HotParams<R>& H, const V4<R>& p)
+{
+    return (grid_axis<R>(P, H, p.x) * P.g_nb + grid_axis<R>(P, H, p.y)) * P.g_nb + grid_axis<R>(P, H, p.z);
+}
 
 template <typename R, int TT>
 __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int i, int slot,
-                                      bool brute, int& overflow)
+                                      int& overflow)
 {
     const V4<R> pi = W.pos[i];
     uint16_t* out = W.nbr + (size_t)slot * maxnb(TT);
     int cnt = 0;
-    const int na = P.na;
-    auto consider = [&](int j) {
-        if (j == i) return;
-        const V4<R> pj = W.pos[j];
-        if (!is_present(pj)) return;
-        const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-        if (dx * dx + dy * dy + dz * dz < H.rlist2) {
-            if (cnt < maxnb(TT)) out[cnt++] = (uint16_t)j;
-            else ++overflow;
-            if (TT == REED_TT_TERSOFF && !is_active(pj) && W.need_map[j] == REED_NO_SLOT)
-                W.need_map[j] = (uint16_t)REED_PENDING;
-        }
-    };
-    if (brute || (W.flags[i] & 1)) {
-        for (int j = 0; j < na; ++j) consider(j);
-    } else {
-        int s[3], b;
-        slot_coords(P, i, s, b);
-        const int n = P.n;
-        const int lo = n >= 3 ? -1 : 0, hi = n >= 3 ? 1 : n - 1;
-        for (int ox = lo; ox <= hi; ++ox) {
-            const int cx = n >= 3 ? pmod(s[0] + ox, n) : ox;
-            for (int oy = lo; oy <= hi; ++oy) {
-                const int cy = n >= 3 ? pmod(s[1] + oy, n) : oy;
-                for (int oz = lo; oz <= hi; ++oz) {
-                    const int cz = n >= 3 ? pmod(s[2] + oz, n) : oz;
-                    const int base = ((cx * n + cy) * n + cz) * P.nb;
-                    for (int q = 0; q < P.nb; ++q)
-                        if (!(W.flags[base + q] & 1)) consider(base + q);
+    const int nb = P.g_nb;
+    const int bx = grid_axis<R>(P, H, pi.x), by = grid_axis<R>(P, H, pi.y), bz = grid_axis<R>(P, H, pi.z);
+    const int z0 = max(bz - 1, 0), z1 = min(bz + 1, nb - 1);
+    for (int cx = max(bx - 1, 0); cx <= min(bx + 1, nb - 1); ++cx) {
+        for (int cy = max(by - 1, 0); cy <= min(by + 1, nb - 1); ++cy) {
+            // bins z0..z1 of one (x, y) column are consecutive in binned[]
+            const int col = (cx * nb + cy) * nb;
+            const int q1 = W.bin_start[col + z1 + 1];
+            for (int q = W.bin_start[col + z0]; q < q1; ++q) {
+                const int j = W.binned[q];
+                if (j == i) continue;
+                const V4<R> pj = W.pos[j];
+                const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                if (dx * dx + dy * dy + dz * dz < H.rlist2) {
+                    if (cnt < maxnb(TT)) out[cnt++] = (uint16_t)j;
+                    else ++overflow;
+                    if (TT == REED_TT_TERSOFF && !is_active(pj) && W.need_map[j] == REED_NO_SLOT)
+                        W.need_map[j] = (uint16_t)REED_PENDING;
                 }
             }
         }
-        const int no = W.S->n_out;
-        for (int k = 0; k < no; ++k) consider(W.outl[k]);
     }
     return cnt;
 }
 
 // Block-wide exclusive prefix sums of two per-thread counts (threads own
-// contiguous chunks of atoms, so the result follows atom order).  Writes
-// each thread's offsets and returns the totals.  All threads must call it.
+// contiguous chunks, so the result follows their order).  Writes each
+// thread's offsets and returns the totals.  All threads must call it.
 template <typename R>
 __device__ __forceinline__ void block_scan2(TrackShared<R>* S, int c0, int c1, int& o0, int& o1, int& t0, int& t1)
 {
@@ -374,65 +386,75 @@ __device__ __forceinline__ void block_scan2(TrackShared<R>* S, int c0, int c1, i
 
 template <typename R, int TT>
 __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow,
-                                 int& cap_overflow, bool force_brute = false)
+                                 int& cap_overflow)
 {
-    const int na = P.na;
+    const int na = P.na, nbins = P.g_nbins;
     TrackShared<R>* S = W.S;
     const int chunk = (na + blockDim.x - 1) / blockDim.x;
     const int i0 = min(na, (int)threadIdx.x * chunk), i1 = min(na, i0 + chunk);
-    // outliers and integrated atoms of this thread's chunk
-    const R disp = R(REED_DISPLACED);
-    int nout = 0, nact = 0;
+    const int bchunk = (nbins + blockDim.x - 1) / blockDim.x;
+    const int j0 = min(nbins, (int)threadIdx.x * bchunk), j1 = min(nbins, j0 + bchunk);
+    // bin populations and integrated atoms of this thread's chunk
+    int nact = 0;
     for (int i = i0; i < i1; ++i) {
         const V4<R> p = W.pos[i];
-        uint8_t fl = 0;
         W.need_map[i] = (uint16_t)REED_NO_SLOT;
         if (is_present(p)) {
-            int s[3], b;
-            slot_coords(P, i, s, b);
-            const R xs[3] = {p.x, p.y, p.z};
-            for (int d = 0; d < 3; ++d) {
-                const int L = S->ion.A[d] - P.half_n;
-                const R lo = R(L + pmod(s[d] - L, P.n) - S->ion.A[d]) * H.a;
-                if (xs[d] < lo - disp || xs[d] > lo + H.a + disp) fl = 1;
-            }
-            nout += fl;
+            atomicAdd(&W.bin_count[grid_bin<R>(P, H, p)], 1u);
             nact += is_active(p) ? 1 : 0;
             W.vel[i].w = R(0);   // path length since the list was built
         }
-        W.flags[i] = fl;
-    }
-    int oo, oa, tot_out, tot_act;
-    block_scan2<R>(S, nout, nact, oo, oa, tot_out, tot_act);
-    for (int i = i0; i < i1; ++i) {
-        const V4<R> p = W.pos[i];
-        if (W.flags[i] & 1) {
-            if (oo < REED_OUTCAP) W.outl[oo] = (uint16_t)i;
-            ++oo;
-        }
-        if (is_active(p)) {
-            if (oa < P.bond_cap) {
-                W.need_map[i] = (uint16_t)oa;
-                W.slot_atom[oa] = (uint16_t)i;
-            } else {
-                ++cap_overflow;
-            }
-            ++oa;
-        }
-    }
-    const int nact_slots = min(tot_act, P.bond_cap);
-    if (threadIdx.x == 0) {
-        S->n_out = min(tot_out, REED_OUTCAP);
-        S->out_ovf = tot_out > REED_OUTCAP;
-        S->active_count = nact_slots;
     }
     __syncthreads();
-    // pair lists reach further than a - 2 REED_DISPLACED: search every atom
-    const bool brute = force_brute || S->out_ovf != 0 || P.nl_brute || TT == REED_TT_BUCKINGHAM;
+    int nbin_atoms = 0;
+    for (int j = j0; j < j1; ++j) nbin_atoms += (int)W.bin_count[j];
+    int ob, oa, tot_b, tot_a;
+    block_scan2<R>(S, nbin_atoms, nact, ob, oa, tot_b, tot_a);
+    for (int j = j0; j < j1; ++j) {
+        W.bin_start[j] = (uint16_t)ob;
+        ob += (int)W.bin_count[j];
+    }
+    if (threadIdx.x == 0) W.bin_start[nbins] = (uint16_t)tot_b;
+    for (int i = i0; i < i1; ++i) {
+        if (!is_active(W.pos[i])) continue;
+        if (oa < P.bond_cap) {
+            W.need_map[i] = (uint16_t)oa;
+            W.slot_atom[oa] = (uint16_t)i;
+        } else {
+            ++cap_overflow;
+        }
+        ++oa;
+    }
+    const int nact_slots = min(tot_a, P.bond_cap);
+    if (threadIdx.x == 0) S->active_count = nact_slots;
+    __syncthreads();
+    // scatter into the bins (the counters run back down to zero)
+    for (int i = i0; i < i1; ++i) {
+        const V4<R> p = W.pos[i];
+        if (!is_present(p)) continue;
+        const int b = grid_bin<R>(P, H, p);
+        const unsigned k = atomicSub(&W.bin_count[b], 1u) - 1u;
+        W.binned[W.bin_start[b] + k] = (uint16_t)i;
+    }
+    __syncthreads();
+    // atom order inside each bin
+    for (int j = threadIdx.x; j < nbins; j += blockDim.x) {
+        const int q0 = W.bin_start[j], q1 = W.bin_start[j + 1];
+        for (int q = q0 + 1; q < q1; ++q) {
+            const uint16_t v = W.binned[q];
+            int r = q - 1;
+            while (r >= q0 && W.binned[r] > v) {
+                W.binned[r + 1] = W.binned[r];
+                --r;
+            }
+            W.binned[r + 1] = v;
+        }
+    }
+    __syncthreads();
     // lists of integrated atoms; their other neighbours become pending
     for (int k = threadIdx.x; k < nact_slots; k += blockDim.x) {
         const int i = W.slot_atom[k];
-        W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, brute, overflow);
+        W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, overflow);
     }
     __syncthreads();
     if constexpr (TT != REED_TT_TERSOFF) {
@@ -462,7 +484,7 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
     __syncthreads();
     for (int k = nact_slots + threadIdx.x; k < nneed; k += blockDim.x) {
         const int i = W.slot_atom[k];
-        W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, brute, overflow);
+        W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, overflow);
     }
     __syncthreads();
     if (threadIdx.x == 0) S->need_count = nneed;
@@ -1008,18 +1030,29 @@ __device__ void initial_forces(const DevParams& P, const HotParams<R>& H, Win<R,
 #include "reed_adjoint.cuh"
 
 // ---------------------------------------------------------------------------
-// The persistent kernel.
+// The persistent kernel.  ADJ (target model NONE only) adds the checkpoints,
+// the step records and the reverse pass of the truncated-segment adjoint.
+// The second launch bound is the number of CTAs per SM the shared memory of
+// the workloads allows, so registers are budgeted for that occupancy.
 // ---------------------------------------------------------------------------
-template <typename R, int TT>
-__global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__ DevParams P,
-                                                         const __grid_constant__ DevBuf B)
+template <typename R, int TT, bool ADJ>
+constexpr int track_min_ctas()
 {
+    if (TT == REED_TT_NONE) return sizeof(R) == 4 ? (ADJ ? 2 : 3) : (ADJ ? 1 : 2);
+    return TT == REED_TT_TERSOFF && sizeof(R) == 4 ? 2 : 1;
+}
+
+template <typename R, int TT, bool ADJ>
+__global__ void __launch_bounds__(256, (track_min_ctas<R, TT, ADJ>())) reed_track_kernel(
+    const __grid_constant__ DevParams P, const __grid_constant__ DevBuf B)
+{
+    static_assert(!ADJ || TT == REED_TT_NONE, "the adjoint runs without target-target forces");
     extern __shared__ __align__(16) unsigned char smem[];
-    Win<R, TT> W(smem, P.na, P.bond_cap, P.adjoint);
+    Win<R, TT> W(smem, P.na, P.bond_cap, ADJ ? 1 : 0, P.g_nbins);
     TrackShared<R>* S = W.S;
     const HotParams<R>& H = hot<R>(P);
     const int tid = threadIdx.x;
-    unsigned char* adjbase = (P.adjoint && B.adj) ? B.adj + (size_t)blockIdx.x * B.adj_stride : nullptr;
+    unsigned char* adjbase = (ADJ && B.adj) ? B.adj + (size_t)blockIdx.x * B.adj_stride : nullptr;
     unsigned char* stack = B.stacks ? B.stacks + (size_t)blockIdx.x * B.stack_stride : nullptr;
 
     // thread-0 counters, flushed at exit
@@ -1038,6 +1071,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
         }
     };
     if (tid == 0) S->top = 0;
+    W.clear_grid(P);
 
     for (;;) {
         // ---- acquire a track: own clone stack first, then a new primary
@@ -1079,7 +1113,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             __syncthreads();
             initial_forces<R, TT>(P, H, W, c_bonds, c_rebuild, nbovf, capovf, wc);
             if constexpr (TT == REED_TT_NONE) {
-                if (adjbase) {   // checkpoint of the state before step 0
+                if (ADJ && adjbase) {   // checkpoint of the state before step 0
                     save_state<R, TT>(P, W, adjbase);
                     __syncthreads();
                 }
@@ -1287,7 +1321,7 @@ __global__ void __launch_bounds__(256) reed_track_kernel(const __grid_constant__
             ++c_tracks;
         }
         __syncthreads();
-        if constexpr (TT == REED_TT_NONE) {
+        if constexpr (ADJ) {
             // truncated-segment sensitivities of the final depth
             if (adjbase && B.grads && S->rec_index >= 0) {
                 double g[REED_NTHETA] = {0, 0, 0, 0, 0, 0, 0, 0};

@@ -142,7 +142,10 @@ typedef struct {
      * target lies beyond it).  With n_initial = 0 the first epoch uses
      * thresholds[] as the initial guess.  A track never sees its depths change. */
     int32_t adaptive;
-    int32_t reserved2;
+    /* 1: a non-adaptive run takes its n_thresholds cloning depths from the
+     * context's device copy set by reed_update_thresholds (thresholds[] is
+     * ignored); the multi-process form of the epoch update. */
+    int32_t device_thresholds;
     int64_t epoch_size;        /* primaries per epoch (adaptive) */
     int64_t n_initial;         /* unenhanced primaries before the first epoch (adaptive) */
     /* Stop handing out primaries once this many tracks (clones included) have
@@ -282,6 +285,22 @@ int reed_trace(reed_ctx* ctx, double* traj, int32_t* anchors, int n_tracks, int 
  * to max_epochs rows of 16 doubles (first n_thresholds valid, +inf = no
  * depth); *n_epochs (host) the number of enhanced epochs run. */
 int reed_thresholds(reed_ctx* ctx, double* history, int max_epochs, int* n_epochs);
+
+/* Set the context's device copy of the cloning depths, read by runs with
+ * opt->device_thresholds = 1.  With hist != NULL (host or device, n_bins + 3
+ * FP64 in the reed_range_profile layout, e.g. the sum of several processes'
+ * range profiles) the first n_thresholds depths are re-estimated from it on
+ * the device exactly as an adaptive run does between epochs (d_k = S^-1(2^-k),
+ * Sec. 2 and the feedback of Sec. 3; an empty histogram leaves them as they
+ * are); else they are copied from thresholds (host, n_thresholds values).
+ * n_bins must be the context's bin count; 1 <= n_thresholds <= 16.  Returns
+ * REED_E_ARG on a bad size, REED_E_CUDA on a device error.  Synchronous. */
+int reed_update_thresholds(reed_ctx* ctx, const double* hist, int n_bins, double bin_width, int n_thresholds,
+                           const double* thresholds);
+
+/* The current device copy of the cloning depths (host or device out, 16
+ * doubles). */
+int reed_get_thresholds(reed_ctx* ctx, double* out16);
 
 /* Zero all tallies, records and counters. */
 int reed_reset(reed_ctx* ctx);

@@ -553,6 +553,11 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
     cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT);
     cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4);
     cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long));
+    {   // no cloning depth until one is set
+        double inf[REED_MAX_THR];
+        for (int k = 0; k < REED_MAX_THR; ++k) inf[k] = HUGE_VAL;
+        cudaMemcpy(ctx->d_thr, inf, sizeof(inf), cudaMemcpyHostToDevice);
+    }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
         reed_destroy(ctx);
         return fail(nullptr, REED_E_CUDA, "%s", cudaGetErrorString(e));
@@ -750,7 +755,7 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
             Pe.first_id = x.first;
             Pe.n_primaries = x.count;
             Pe.nthr = x.nthr;
-            Pe.thr_from_device = (o.adaptive && x.nthr > 0) ? 1 : 0;
+            Pe.thr_from_device = ((o.adaptive || o.device_thresholds) && x.nthr > 0) ? 1 : 0;
             if ((e = cudaMemsetAsync(ctx->d_next, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
             if (o.adaptive && x.nthr > 0) {
                 double* hrow = ctx->d_thr_hist + (size_t)REED_MAX_THR * row++;
@@ -977,6 +982,38 @@ int reed_thresholds(reed_ctx* ctx, double* history, int max_epochs, int* n_epoch
     const int m = std::min(max_epochs, ctx->thr_epochs);
     if (m > 0 && history)
         CK(cudaMemcpy(history, ctx->d_thr_hist, sizeof(double) * REED_MAX_THR * m, cudaMemcpyDefault));
+    return REED_OK;
+}
+
+int reed_update_thresholds(reed_ctx* ctx, const double* hist, int n_bins, double bin_width, int n_thresholds,
+                           const double* thresholds)
+{
+    if (!ctx || n_thresholds < 1 || n_thresholds > REED_MAX_THR) return REED_E_ARG;
+    if (hist) {
+        if (n_bins < 1 || !(bin_width > 0)) return fail(ctx, REED_E_ARG, "need n_bins >= 1 and bin_width > 0");
+        const size_t need = sizeof(double) * ((size_t)n_bins + 3);
+        if (need > ctx->kde_bytes) {
+            if (ctx->d_kde) cudaFree(ctx->d_kde);
+            ctx->d_kde = nullptr;
+            ctx->kde_bytes = 0;
+            CK(cudaMalloc((void**)&ctx->d_kde, need));
+            ctx->kde_bytes = need;
+        }
+        CK(cudaMemcpy(ctx->d_kde, hist, need, cudaMemcpyDefault));
+        update_thresholds_kernel<<<1, 1>>>(ctx->d_kde, n_bins, bin_width, n_thresholds, ctx->d_thr, nullptr);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+    } else {
+        if (!thresholds) return REED_E_ARG;
+        CK(cudaMemcpy(ctx->d_thr, thresholds, sizeof(double) * n_thresholds, cudaMemcpyHostToDevice));
+    }
+    return REED_OK;
+}
+
+int reed_get_thresholds(reed_ctx* ctx, double* out16)
+{
+    if (!ctx || !out16) return REED_E_ARG;
+    CK(cudaMemcpy(out16, ctx->d_thr, sizeof(double) * REED_MAX_THR, cudaMemcpyDefault));
     return REED_OK;
 }
 
@@ -1258,7 +1295,8 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     if (o.ctas_per_sm < 0) return fail(nullptr, REED_E_ARG, "negative ctas_per_sm");
     if (o.record_tracks || o.trace_tracks || o.trace_steps)
         return fail(nullptr, REED_E_ARG, "reed_run_static keeps no per-track records or traces");
-    if (o.adaptive) return fail(nullptr, REED_E_ARG, "reed_run_static runs fixed cloning depths only");
+    if (o.adaptive || o.device_thresholds)
+        return fail(nullptr, REED_E_ARG, "reed_run_static runs fixed cloning depths only");
     if (o.damage_n) return fail(nullptr, REED_E_ARG, "reed_run_static keeps no damage map");
     if (o.adjoint) return fail(nullptr, REED_E_ARG, "reed_run_static computes no sensitivities");
 

@@ -49,7 +49,7 @@ class reed_run_opts(C.Structure):
                 ("bin_width", C.c_double), ("first_id", C.c_int64), ("threads_per_track", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("record_tracks", C.c_int32), ("trace_tracks", C.c_int32),
                 ("trace_steps", C.c_int32), ("reserved", C.c_int32), ("record_capacity", C.c_int64),
-                ("stream", C.c_void_p), ("adaptive", C.c_int32), ("reserved2", C.c_int32),
+                ("stream", C.c_void_p), ("adaptive", C.c_int32), ("device_thresholds", C.c_int32),
                 ("epoch_size", C.c_int64), ("n_initial", C.c_int64), ("target_tracks", C.c_int64),
                 ("damage_n", C.c_int32), ("reserved3", C.c_int32), ("damage_voxel", C.c_double),
                 ("damage_min", C.c_double), ("adjoint", C.c_int32), ("adj_segment", C.c_int32),
@@ -84,7 +84,7 @@ class reed_stats_t(C.Structure):
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",
             "reed_reset", "reed_last_error", "reed_destroy", "reed_philox", "reed_cell_atoms", "reed_forces",
             "reed_window_replay", "reed_run_static", "reed_thresholds", "reed_damage_map", "reed_track_grads",
-            "reed_kde_profile", "reed_grad", "reed_set_theta"]
+            "reed_kde_profile", "reed_grad", "reed_set_theta", "reed_update_thresholds", "reed_get_thresholds"]
 
 _LIB = None
 _D = C.POINTER(C.c_double)
@@ -126,6 +126,8 @@ def lib():
         L.reed_kde_profile.argtypes = [vp, C.c_double, C.c_int, C.c_double, vp]
         L.reed_grad.argtypes = [vp, C.c_double, C.c_int, C.c_double, vp, vp]
         L.reed_set_theta.argtypes = [vp, _D]
+        L.reed_update_thresholds.argtypes = [vp, vp, C.c_int, C.c_double, C.c_int, _D]
+        L.reed_get_thresholds.argtypes = [vp, vp]
         L.reed_last_error.argtypes = [vp]
         L.reed_last_error.restype = C.c_char_p
         L.reed_destroy.argtypes = [vp]
@@ -184,13 +186,14 @@ def potentials_struct(w) -> reed_potentials:
 
 def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, record=True, record_capacity=0,
              trace_tracks=0, trace_steps=0, stream=None, adaptive=False, epoch_size=4096, n_initial=50,
-             target_tracks=0, damage=True, adjoint=False, adj_segment=200, adj_every=20, nl_skin=0.0) -> reed_run_opts:
+             target_tracks=0, damage=True, adjoint=False, adj_segment=200, adj_every=20, nl_skin=0.0,
+             device_thresholds=False, thresholds=None) -> reed_run_opts:
     o = reed_run_opts()
     o.dt_max_fs, o.dx_max, o.e_stop = w["dt_max_fs"], w["dx_max"], w["e_stop"]
     o.step_cap = int(w["step_cap"])
     o.beam_mode = BEAM[w["beam_mode"]]
     o.precision = precision
-    thr = list(w["thresholds"])
+    thr = list(w["thresholds"] if thresholds is None else thresholds)
     o.n_thresholds = len(thr)
     for i, d in enumerate(thr):
         o.thresholds[i] = d
@@ -202,6 +205,7 @@ def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, reco
     o.trace_tracks, o.trace_steps = trace_tracks, trace_steps
     o.stream = stream
     o.adaptive = 1 if adaptive else 0
+    o.device_thresholds = 1 if device_thresholds else 0
     o.epoch_size, o.n_initial, o.target_tracks = epoch_size, n_initial, target_tracks
     o.damage_n = int(w.get("damage_n", 0)) if damage else 0
     o.damage_voxel, o.damage_min = float(w.get("damage_voxel", 10.0)), float(w.get("damage_min", 0.1))
@@ -302,6 +306,22 @@ def reed_set_theta(ctx, theta):
     t = np.ascontiguousarray(theta, dtype=np.float64)
     assert t.size == 8
     _check(lib().reed_set_theta(ctx, t.ctypes.data_as(_D)), ctx)
+
+
+def reed_update_thresholds(ctx, n_thresholds, hist_ptr=None, n_bins=0, bin_width=0.0, thresholds=None):
+    """Set the device cloning depths: re-estimated from a range profile at
+    hist_ptr (host or device address), or copied from `thresholds`."""
+    t = None
+    if thresholds is not None:
+        t = np.ascontiguousarray(thresholds, dtype=np.float64)
+    _check(lib().reed_update_thresholds(ctx, hist_ptr, n_bins, bin_width, n_thresholds,
+                                        t.ctypes.data_as(_D) if t is not None else None), ctx)
+
+
+def reed_get_thresholds(ctx):
+    out = np.zeros(16)
+    _check(lib().reed_get_thresholds(ctx, out.ctypes.data), ctx)
+    return out
 
 
 def reed_reset(ctx):

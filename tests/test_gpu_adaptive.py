@@ -87,3 +87,24 @@ def test_stop_rule_completes_started_lineages(R):
     # every primary handed out was followed with all its clones
     wts = np.ldexp(1.0, -rec["level"].astype(int))
     assert np.sum(wts) == st["primaries"]
+
+
+def test_sharded_driver_matches_adaptive_run(R):
+    # the multi-process driver on one rank: depths re-estimated through
+    # reed_update_thresholds between separate runs equal the in-graph epochs
+    from paper_0810_4737_gb300 import sharded
+    w = workload("b1kev_si_0k_zbl", **W)
+    n, epoch, ninit = 1250, 400, 50
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n, seed=9, adaptive=True, n_initial=ninit, epoch_size=epoch)
+        ref_bins, ref_extra = ctx.profile()
+        ref_th = ctx.thresholds()
+        ref_st = ctx.stats()
+    with R.Reed(w) as ctx:
+        eng = sharded.ReedShard(ctx, seed=9)
+        hist = sharded.run_adaptive(eng, n, epoch, ninit, w["thresholds"])
+        bins, extra = ctx.profile()
+        st = ctx.stats()
+    assert np.array_equal(np.array(hist), ref_th[:, :6])
+    assert np.array_equal(bins, ref_bins) and np.array_equal(extra, ref_extra)
+    assert st["tracks"] == ref_st["tracks"] and st["steps"] == ref_st["steps"]

@@ -35,6 +35,10 @@ WORKLOAD = "as10kev_si_300k_tersoff"
 # 35 ops, integrated atom update 12 FMA = 24 ops, Tersoff bond-angle triplet 60 ops.
 OPS_PAIR, OPS_MOVE, OPS_TRIPLET = 35, 24, 60
 SMS, FP32_LANES = 152, 128
+# DRAM bytes (read + write) per ion-step of the stepper kernel from the ncu
+# capture summarised in profiles/reed_track_kernel_tersoff_as10kev.md (None
+# when the kernel has changed since).
+TRAFFIC_PER_ION_STEP = None
 
 
 def _dist():
@@ -190,6 +194,8 @@ def main():
     for i in range(args.warmup):
         one(i)
     ctx.reset()
+    # measured throughput of the units that bound the stepper (roofline denominators)
+    peaks = R.reed_peaks() if rank == 0 else None
     # ---- timed region: K steps, device-timed with CUDA events on the launch stream
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -225,7 +231,7 @@ def main():
     flops = OPS_PAIR * st["pair_evals"] + OPS_MOVE * st["atom_updates"] + OPS_TRIPLET * st["triplets"]
     kern_s = sum(kernel_ms) * 1e-3
     achieved = flops / kern_s / 1e12
-    peak = SMS * FP32_LANES * 2 * 2070e6 / 1e12
+    derived = SMS * FP32_LANES * 2 * 2070e6 / 1e12
     # ---- end to end through the public API with host buffers
     e2e = None
     if rank == 0:
@@ -265,9 +271,11 @@ def main():
         threads = os.cpu_count() or 1
         ci = args.cpu_ions or threads
         v, stp, dt = cpu_baseline(w, ci, threads, args.cpu_steps)
+        v1, stp1, dt1 = cpu_baseline(w, 1, 1, args.cpu_steps // 2)
         cpu = {"value": v, "unit": "ion-steps/s", "cores": threads, "kind": "oracle",
                "sample": "%d primaries of %s, first %d steps each (%d ion-steps, %.1f s); FP64 C oracle, OpenMP"
-                         % (ci, w["name"], args.cpu_steps, stp, dt)}
+                         % (ci, w["name"], args.cpu_steps, stp, dt),
+               "one_thread": {"value": v1, "sample": "1 primary, first %d steps (%.1f s)" % (stp1, dt1)}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "ion-steps/s", "n_gpus": ws, "steps": args.steps,
@@ -281,11 +289,14 @@ def main():
             "pair_forces_per_s": pairs_per_s,
             "gpu_launches": args.steps,
             "clocks": clk,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp32_tflops"], "traffic": TRAFFIC_PER_ION_STEP * steps_done / ws
+                         / args.steps if TRAFFIC_PER_ION_STEP is not None else None,
+                         "peak_source": "measured FP32 FMA stream (reed_peaks, burst) at %.0f MHz; derived "
+                                        "152 SM x 128 lanes x 2 x 2070 MHz = %.1f" % (peaks["sm_mhz"], derived),
                          "kernel": "reed_track_kernel<float, TERSOFF>",
                          "kernel_ms_per_launch": sum(kernel_ms) / len(kernel_ms)},
+            "peaks": peaks,
             "fp64_path": fp64,
             "cpu_baseline": cpu,
             "e2e": e2e,

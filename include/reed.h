@@ -302,6 +302,21 @@ int reed_update_thresholds(reed_ctx* ctx, const double* hist, int n_bins, double
  * doubles). */
 int reed_get_thresholds(reed_ctx* ctx, double* out16);
 
+/* Measured throughput of the units that bound the track stepper, on the
+ * current device (microbenchmarks of independent instruction streams, a few
+ * tenths of a second in all): FP32 and FP64 FMA, the SFU's ex2 and rsqrt,
+ * 128-bit shared-memory loads, and the SM clock seen while they ran.  The
+ * denominators of the stepper's roofline (no paper counterpart). */
+typedef struct {
+    double fp32_tflops, fp64_tflops;   /* FMA = 2 FLOP */
+    double ex2_gops, rsqrt_gops;       /* SFU results per second (1e9) */
+    double smem_tbs;                   /* shared-memory load bandwidth, TB/s */
+    double sm_mhz;                     /* clock64 cycles per second during the run */
+    int32_t sms, reserved;
+} reed_peaks_t;
+
+int reed_peaks(reed_peaks_t* out);
+
 /* Zero all tallies, records and counters. */
 int reed_reset(reed_ctx* ctx);
 

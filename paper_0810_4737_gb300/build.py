@@ -1,7 +1,7 @@
 """Build the CUDA library ``libreed.so`` in-tree for sm_103a (GB300).
 
-The three translation units (host C ABI, FP32 kernels, FP64 kernels) are
-compiled in parallel with nvcc and linked into
+The four translation units (host C ABI, FP32 kernels, FP64 kernels, the
+throughput microbenchmarks) are compiled in parallel with nvcc and linked into
 ``paper_0810_4737_gb300/_build/libreed.so``.
 """
 from __future__ import annotations
@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libreed.so")
-SOURCES = ["reed_capi.cu", "reed_kernels_f32.cu", "reed_kernels_f64.cu"]
+SOURCES = ["reed_capi.cu", "reed_kernels_f32.cu", "reed_kernels_f64.cu", "reed_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

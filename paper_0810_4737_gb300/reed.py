@@ -66,6 +66,11 @@ RECORD_DTYPE = np.dtype([("id", "<u8"), ("primary", "<u8"), ("z", "<f8"), ("t", 
                          ("steps", "<i8"), ("level", "<i4"), ("status", "<i4")])
 
 
+class reed_peaks_t(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("fp32_tflops", "fp64_tflops", "ex2_gops", "rsqrt_gops", "smem_tbs",
+                                          "sm_mhz")] + [("sms", C.c_int32), ("reserved", C.c_int32)]
+
+
 class reed_stats_t(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "primaries", "clones", "tracks", "steps", "pair_evals", "bond_evals", "shifts", "rebuilds",
@@ -84,7 +89,7 @@ class reed_stats_t(C.Structure):
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",
             "reed_reset", "reed_last_error", "reed_destroy", "reed_philox", "reed_cell_atoms", "reed_forces",
             "reed_window_replay", "reed_run_static", "reed_thresholds", "reed_damage_map", "reed_track_grads",
-            "reed_kde_profile", "reed_grad", "reed_set_theta", "reed_update_thresholds", "reed_get_thresholds"]
+            "reed_kde_profile", "reed_grad", "reed_set_theta", "reed_update_thresholds", "reed_get_thresholds", "reed_peaks"]
 
 _LIB = None
 _D = C.POINTER(C.c_double)
@@ -128,6 +133,7 @@ def lib():
         L.reed_set_theta.argtypes = [vp, _D]
         L.reed_update_thresholds.argtypes = [vp, vp, C.c_int, C.c_double, C.c_int, _D]
         L.reed_get_thresholds.argtypes = [vp, vp]
+        L.reed_peaks.argtypes = [C.POINTER(reed_peaks_t)]
         L.reed_last_error.argtypes = [vp]
         L.reed_last_error.restype = C.c_char_p
         L.reed_destroy.argtypes = [vp]
@@ -322,6 +328,13 @@ def reed_get_thresholds(ctx):
     out = np.zeros(16)
     _check(lib().reed_get_thresholds(ctx, out.ctypes.data), ctx)
     return out
+
+
+def reed_peaks() -> dict:
+    """Measured FP32/FP64/SFU/shared-memory throughput of the current GPU."""
+    p = reed_peaks_t()
+    _check(lib().reed_peaks(C.byref(p)), None)
+    return {n: getattr(p, n) for n, _ in reed_peaks_t._fields_ if n != "reserved"}
 
 
 def reed_reset(ctx):

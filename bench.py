@@ -187,6 +187,8 @@ def main():
 
     ctx = R.Reed(w)
     first = rank * 10_000_000
+    # launch configuration: timed trials of every candidate (not part of a step)
+    tune = ctx.autotune(n_trial=2 * 152 * 2, seed=w["seed"] + 1, step_cap=1500, stream=None)
 
     def one(step_idx, record=False):
         return ctx.run(n_ions=n, seed=w["seed"], first_id=first + step_idx * n, record=record, stream=sh)
@@ -287,6 +289,7 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)",
                        "precision": "FP32 forces/atoms, FP64 ion position/time/energy accumulation"},
             "pair_forces_per_s": pairs_per_s,
+            "autotune": [{"threads_per_track": t, "ctas_per_sm": c, "ion_steps_per_s": v} for t, c, v in tune],
             "gpu_launches": args.steps,
             "clocks": clk,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",

@@ -302,6 +302,26 @@ int reed_update_thresholds(reed_ctx* ctx, const double* hist, int n_bins, double
  * doubles). */
 int reed_get_thresholds(reed_ctx* ctx, double* out16);
 
+/* Launch-configuration autotuner (the batching form's tuning): runs
+ * n_trial primaries of the given beam (ids from 2^40 up, so no primary of a
+ * real run is repeated) once per candidate -- threads_per_track in {32, 64,
+ * 128, 256} and, for each, CTAs per SM at the occupancy maximum, three
+ * quarters and half of it -- and keeps the fastest (ion-steps per second of
+ * kernel time) for later runs of this context whose opt->threads_per_track
+ * and opt->ctas_per_sm are 0 and whose precision and adjoint flag match opt.
+ * The trials run in a private context, so this context's tallies are not
+ * touched; records, traces, damage and cloning are off in them, and
+ * opt->step_cap bounds each trial track.  table (host, may be NULL) receives up
+ * to cap timed candidates, *n_out (host, may be NULL) their number. */
+typedef struct {
+    int32_t threads_per_track, ctas_per_sm;
+    double ion_steps_per_s;
+} reed_tune_entry;
+
+int reed_autotune(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double tilt_deg, double rot_deg_lo,
+                  double rot_deg_hi, int64_t n_trial, uint64_t seed, const reed_run_opts* opt, reed_tune_entry* table,
+                  int cap, int* n_out);
+
 /* Measured throughput of the units that bound the track stepper, on the
  * current device (microbenchmarks of independent instruction streams, a few
  * tenths of a second in all): FP32 and FP64 FMA, the SFU's ex2 and rsqrt,

@@ -31,6 +31,12 @@
  * Where the paper defers to its references, the readings taken are listed in
  * the project's design notes; each is marked "reading:" below.
  *
+ * Parity unpinned: the magnitude of the Lindhard-Scharff drag coefficient
+ * (o_gamma_ls) and the Buckingham parameter values are readings with no
+ * independent published number to test against; only their use (the drag's
+ * closed-form range, Buckingham forces against finite differences and the
+ * fluorite symmetry) is pinned.
+ *
  * Units: Angstrom, eV, amu; time unit tau = sqrt(amu A^2 / eV) = 10.1805 fs.
  */
 #include <math.h>

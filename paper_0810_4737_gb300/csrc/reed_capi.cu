@@ -91,6 +91,9 @@ struct reed_ctx {
     int thr_hist_cap = 0, thr_epochs = 0;
     unsigned long long* d_finished = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    // autotuned launch configuration per [precision][adjoint] (0 = none)
+    int tuned_threads[2][2] = {{0, 0}, {0, 0}};
+    int tuned_ctas[2][2] = {{0, 0}, {0, 0}};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0.0;
     LaunchCfg last_cfg{};
@@ -653,13 +656,16 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
         return fail(ctx, REED_E_SMEM, "window of %d atoms needs %zu B of shared memory (max %zu)", P.na, smem,
                     ctx->smem_optin);
     LaunchCfg L;
-    L.threads = o.threads_per_track ? o.threads_per_track : (tt == REED_TT_NONE ? 64 : 256);
+    const int pi = f64 ? 1 : 0, ai = P.adjoint ? 1 : 0;
+    const bool tuned = !o.threads_per_track && !o.ctas_per_sm && ctx->tuned_threads[pi][ai] > 0;
+    L.threads = o.threads_per_track ? o.threads_per_track
+                                    : (tuned ? ctx->tuned_threads[pi][ai] : (tt == REED_TT_NONE ? 64 : 256));
     L.smem = smem;
     int occ = 0;
     CK(f64 ? reed_f64::occupancy(tt, L.threads, smem, &occ, P.adjoint)
            : reed_f32::occupancy(tt, L.threads, smem, &occ, P.adjoint));
     if (occ < 1) return fail(ctx, REED_E_SMEM, "kernel does not fit on an SM (%zu B shared, %d threads)", smem, L.threads);
-    L.ctas_per_sm = o.ctas_per_sm ? std::min(o.ctas_per_sm, occ) : occ;
+    L.ctas_per_sm = o.ctas_per_sm ? std::min(o.ctas_per_sm, occ) : (tuned ? std::min(ctx->tuned_ctas[pi][ai], occ) : occ);
     L.grid = ctx->sms * L.ctas_per_sm;
 
     // clone stacks: one record per cloning level per CTA
@@ -1052,6 +1058,75 @@ void reed_destroy(reed_ctx* ctx)
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
+}
+
+int reed_autotune(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double tilt_deg, double rot_deg_lo,
+                  double rot_deg_hi, int64_t n_trial, uint64_t seed, const reed_run_opts* opt, reed_tune_entry* table,
+                  int cap, int* n_out)
+{
+    if (!ctx || !opt || n_trial < 1 || cap < 0) return REED_E_ARG;
+    if (n_out) *n_out = 0;
+    reed_ctx* t = nullptr;
+    int rc = reed_init(&t, &ctx->lat, ctx->sp, ctx->nspec, &ctx->pot);
+    if (rc) return fail(ctx, rc, "autotune: %s", g_init_error.c_str());
+    reed_run_opts o = *opt;
+    o.record_tracks = 0;
+    o.trace_tracks = 0;
+    o.trace_steps = 0;
+    o.adaptive = 0;
+    o.device_thresholds = 0;
+    o.n_thresholds = 0;
+    o.damage_n = 0;
+    o.target_tracks = 0;
+    o.first_id = (int64_t)1 << 40;
+    const int pi = opt->precision == REED_PREC_FP64 ? 1 : 0, ai = opt->adjoint ? 1 : 0;
+    if (ai) o.record_tracks = 1;
+    int best_t = 0, best_c = 0, n = 0;
+    double best = -1.0;
+    static const int kThreads[4] = {32, 64, 128, 256};
+    for (int ti = 0; ti < 4; ++ti) {
+        // the occupancy maximum for this thread count: a run with ctas_per_sm
+        // far above it is clamped to it
+        reed_run_opts probe = o;
+        probe.threads_per_track = kThreads[ti];
+        probe.ctas_per_sm = 1 << 20;
+        probe.step_cap = 1;
+        reed_reset(t);
+        rc = reed_run(t, ion_Z, ion_M, energy_eV, tilt_deg, rot_deg_lo, rot_deg_hi, 1, seed, &probe);
+        if (rc < 0) continue;   // does not fit (shared memory / threads)
+        o.threads_per_track = kThreads[ti];
+        const int occ = t->last_cfg.ctas_per_sm;
+        int cands[3] = {occ, (3 * occ + 3) / 4, (occ + 1) / 2};
+        for (int ci = 0; ci < 3; ++ci) {
+            const int c = cands[ci];
+            bool dup = false;
+            for (int k = 0; k < ci; ++k) dup |= cands[k] == c;
+            if (dup || c < 1) continue;
+            o.ctas_per_sm = c;
+            reed_reset(t);
+            rc = reed_run(t, ion_Z, ion_M, energy_eV, tilt_deg, rot_deg_lo, rot_deg_hi, n_trial, seed, &o);
+            if (rc < 0) {
+                reed_destroy(t);
+                return fail(ctx, rc, "autotune trial (%d threads, %d CTAs/SM) failed", kThreads[ti], c);
+            }
+            reed_stats_t st;
+            reed_stats(t, &st);
+            const double v = st.kernel_ms > 0 ? (double)st.steps / (st.kernel_ms * 1e-3) : 0.0;
+            if (table && n < cap) table[n] = {kThreads[ti], c, v};
+            ++n;
+            if (v > best) {
+                best = v;
+                best_t = kThreads[ti];
+                best_c = c;
+            }
+        }
+    }
+    reed_destroy(t);
+    if (n_out) *n_out = n;
+    if (best_t == 0) return fail(ctx, REED_E_SMEM, "autotune: no launch configuration fits");
+    ctx->tuned_threads[pi][ai] = best_t;
+    ctx->tuned_ctas[pi][ai] = best_c;
+    return REED_OK;
 }
 
 // ---- diagnostics -------------------------------------------------------

@@ -71,6 +71,10 @@ class reed_peaks_t(C.Structure):
                                           "sm_mhz")] + [("sms", C.c_int32), ("reserved", C.c_int32)]
 
 
+class reed_tune_entry(C.Structure):
+    _fields_ = [("threads_per_track", C.c_int32), ("ctas_per_sm", C.c_int32), ("ion_steps_per_s", C.c_double)]
+
+
 class reed_stats_t(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "primaries", "clones", "tracks", "steps", "pair_evals", "bond_evals", "shifts", "rebuilds",
@@ -89,7 +93,7 @@ class reed_stats_t(C.Structure):
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",
             "reed_reset", "reed_last_error", "reed_destroy", "reed_philox", "reed_cell_atoms", "reed_forces",
             "reed_window_replay", "reed_run_static", "reed_thresholds", "reed_damage_map", "reed_track_grads",
-            "reed_kde_profile", "reed_grad", "reed_set_theta", "reed_update_thresholds", "reed_get_thresholds", "reed_peaks"]
+            "reed_kde_profile", "reed_grad", "reed_set_theta", "reed_update_thresholds", "reed_get_thresholds", "reed_peaks", "reed_autotune"]
 
 _LIB = None
 _D = C.POINTER(C.c_double)
@@ -134,6 +138,8 @@ def lib():
         L.reed_update_thresholds.argtypes = [vp, vp, C.c_int, C.c_double, C.c_int, _D]
         L.reed_get_thresholds.argtypes = [vp, vp]
         L.reed_peaks.argtypes = [C.POINTER(reed_peaks_t)]
+        L.reed_autotune.argtypes = [vp] + [C.c_double] * 6 + [C.c_int64, C.c_uint64, C.POINTER(reed_run_opts),
+                                                              C.POINTER(reed_tune_entry), C.c_int, _I32]
         L.reed_last_error.argtypes = [vp]
         L.reed_last_error.restype = C.c_char_p
         L.reed_destroy.argtypes = [vp]
@@ -439,6 +445,19 @@ class Reed:
 
     def reset(self):
         reed_reset(self.ctx)
+
+    def autotune(self, n_trial, seed=None, precision=PREC_MIXED, **kw):
+        """Time the launch configurations on n_trial primaries and keep the
+        fastest for later runs; returns [(threads, ctas_per_sm, ion-steps/s)]."""
+        w = self.w
+        o = run_opts(w, precision=precision, **kw)
+        ion = w["ion"]
+        tab = (reed_tune_entry * 16)()
+        n = C.c_int32(0)
+        _check(lib().reed_autotune(self.ctx, ion["Z"], ion["M"], w["energy"], w["tilt"], w["rot"][0], w["rot"][1],
+                                   n_trial, w["seed"] if seed is None else seed, C.byref(o), tab, 16, C.byref(n)),
+               self.ctx)
+        return [(tab[i].threads_per_track, tab[i].ctas_per_sm, tab[i].ion_steps_per_s) for i in range(n.value)]
 
     def thresholds(self):
         return reed_thresholds(self.ctx)

@@ -187,3 +187,20 @@ def test_step_cap_truncates(R):
     assert st["truncated"] + st["backscattered"] + st["stopped"] == 16
     assert np.all(rec["steps"][rec["status"] == 3] == 100)
     assert st["truncated"] > 0
+
+
+def test_autotune_keeps_the_fastest_and_results_do_not_change(R):
+    w = workload("b1kev_si_0k_zbl", sigma=0.076, rot=(0.0, 45.0))
+    with R.Reed(w) as ctx:
+        tab = ctx.autotune(n_trial=600, seed=11, step_cap=400)
+        assert len(tab) >= 4 and all(v > 0 for _, _, v in tab)
+        best = max(tab, key=lambda e: e[2])
+        ctx.run(n_ions=300, seed=2)
+        st = ctx.stats()
+        assert (st["threads_per_track"], st["ctas_per_sm"]) == best[:2]
+        tuned = ctx.records()
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=300, seed=2, threads=256, ctas_per_sm=1)
+        plain = ctx.records()
+    a, b = np.sort(tuned, order="id"), np.sort(plain, order="id")
+    assert np.array_equal(a, b)

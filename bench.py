@@ -41,6 +41,21 @@ SMS, FP32_LANES = 152, 128
 TRAFFIC_PER_ION_STEP = None
 
 
+def _ion_name(w):
+    return {5.0: "B-11", 33.0: "As-75", 18.0: "Ar-40"}.get(w["ion"]["Z"], "Z=%g" % w["ion"]["Z"])
+
+
+def _target_name(w):
+    base = "Si(100)" if w["lattice"] == "diamond" else "CeO2 fluorite"
+    temp = "300 K sigma %.3f A" % w["sigma"] if w["sigma"] > 0 else "0 K"
+    model = {"none": "ZBL ion-target only", "tersoff": "Tersoff+ZBL", "buckingham": "Buckingham+ZBL"}[w["tt"]]
+    return "%s %s, %s" % (base, temp, model)
+
+
+def _window_atoms(w):
+    return w["n"] ** 3 * (8 if w["lattice"] == "diamond" else 12)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -139,8 +154,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ion-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "ions_per_step": n, "ion": "As-75", "energy_eV": w["energy"],
-                       "window_atoms": w["n"] ** 3 * 8,
+            "config": {"workload": w["name"], "ions_per_step": n, "ion": _ion_name(w), "energy_eV": w["energy"],
+                       "target": _target_name(w), "window_atoms": _window_atoms(w),
                        "sample": "%d primaries x first %d steps per step" % (n, args.cpu_steps)},
             "cpu_baseline": {"value": value, "unit": "ion-steps/s", "cores": threads, "kind": "oracle",
                              "sample": "%d primaries of %s, first %d steps each, per step; FP64 C oracle, OpenMP"
@@ -163,6 +178,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1200, help="oracle sample: steps per primary")
     ap.add_argument("--ref-ions", type=int, default=0, help="reference arm primaries per step (0: one per core)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, help="threads per track (0: autotune)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="CTAs per SM (0: autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -187,11 +204,14 @@ def main():
 
     ctx = R.Reed(w)
     first = rank * 10_000_000
-    # launch configuration: timed trials of every candidate (not part of a step)
-    tune = ctx.autotune(n_trial=2 * 152 * 2, seed=w["seed"] + 1, step_cap=1500, stream=None)
+    # launch configuration: given, or timed trials of every candidate (not part of a step)
+    tune = []
+    if not (args.threads and args.ctas_per_sm):
+        tune = ctx.autotune(n_trial=2 * 152 * 2, seed=w["seed"] + 1, step_cap=1500, stream=None)
+    launch = dict(threads=args.threads, ctas_per_sm=args.ctas_per_sm)
 
     def one(step_idx, record=False):
-        return ctx.run(n_ions=n, seed=w["seed"], first_id=first + step_idx * n, record=record, stream=sh)
+        return ctx.run(n_ions=n, seed=w["seed"], first_id=first + step_idx * n, record=record, stream=sh, **launch)
 
     for i in range(args.warmup):
         one(i)
@@ -241,7 +261,7 @@ def main():
         t0 = time.perf_counter()
         e2e_steps = 0
         for i in range(args.steps):
-            ctx.run(n_ions=n, seed=w["seed"], first_id=first + (100 + i) * n, record=False)
+            ctx.run(n_ions=n, seed=w["seed"], first_id=first + (100 + i) * n, record=False, **launch)
             bins, extra = ctx.profile()                 # device -> host
             e2e_steps = ctx.stats()["steps"]            # device -> host
         dt = time.perf_counter() - t0
@@ -283,8 +303,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "ion-steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w["name"], "ions_per_step_per_gpu": n, "ion": "As-75", "energy_eV": w["energy"],
-                       "target": "Si(100) 300 K sigma 0.076 A, Tersoff+ZBL", "window_atoms": w["n"] ** 3 * 8,
+            "config": {"workload": w["name"], "ions_per_step_per_gpu": n, "ion": _ion_name(w), "energy_eV": w["energy"],
+                       "target": _target_name(w), "window_atoms": _window_atoms(w),
                        "parallelism": "replicas (independent primaries per GPU)",
                        "l2": "flushed between timed steps (256 MB write)",
                        "precision": "FP32 forces/atoms, FP64 ion position/time/energy accumulation"},
@@ -297,7 +317,7 @@ def main():
                          / args.steps if TRAFFIC_PER_ION_STEP is not None else None,
                          "peak_source": "measured FP32 FMA stream (reed_peaks, burst) at %.0f MHz; derived "
                                         "152 SM x 128 lanes x 2 x 2070 MHz = %.1f" % (peaks["sm_mhz"], derived),
-                         "kernel": "reed_track_kernel<float, TERSOFF>",
+                         "kernel": "reed_track_kernel<float, %s>" % w["tt"].upper(),
                          "kernel_ms_per_launch": sum(kernel_ms) / len(kernel_ms)},
             "peaks": peaks,
             "fp64_path": fp64,

@@ -497,22 +497,30 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
 
 // Tersoff pass 1 for the atom in list slot k: for each bond (a, b) store
 // {pre_ab = 1/2 dV_ab/db * db/dzeta_ab, dV_ab/dr}; returns 1/2 sum_b V_ab.
+// For an integrated atom (k < active_count) it also writes to frc[a] the
+// part of the force on a that its own bonds give: the radial terms
+// 1/2 dV_ab/dr and a as the centre of every zeta_ab (the derivative of zeta
+// with respect to x_a is summed alongside zeta itself).
 template <typename R, int TT>
 __device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned long long& triplets)
 {
     const int a = W.slot_atom[k];
     const int m = W.nnb[k], cs = W.cap;
+    const bool own = k < W.S->active_count;
     const uint16_t* nb = W.nbr + k;   // neighbour q at nb[q * cs]
     V2<R>* bond = W.bond + k;
     const V4<R> pa = W.pos[a];
     R E = R(0);
+    R fx = R(0), fy = R(0), fz = R(0);
     for (int q = 0; q < m; ++q) {
         const V4<R> pq = W.pos[nb[q * cs]];
         const R qx = pq.x - pa.x, qy = pq.y - pa.y, qz = pq.z - pa.z;
         const R r2q = qx * qx + qy * qy + qz * qz;
         const R irq = Mth<R>::rsqrt(r2q);
         const R rq = r2q * irq;
+        const R ux = qx * irq, uy = qy * irq, uz = qz * irq;   // unit a -> q
         R zeta = R(0);
+        R dx = R(0), dy = R(0), dz = R(0);   // d zeta / d x_a
         for (int p = 0; p < m; ++p) {
             if (p == q) continue;
             const V4<R> pk = W.pos[nb[p * cs]];
@@ -521,11 +529,23 @@ __device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned lo
             const R irk = Mth<R>::rsqrt(r2k);
             R dfc;
             const R fck = ters_fc<R>(H, r2k * irk, dfc);
-            if (fck <= R(0)) continue;
-            const R c = (qx * kx + qy * ky + qz * kz) * irq * irk;
+            if (fck <= R(0) && dfc == R(0)) continue;
+            const R vx = kx * irk, vy = ky * irk, vz = kz * irk;   // unit a -> p
+            const R c = ux * vx + uy * vy + uz * vz;
             R dg;
-            zeta += fck * ters_g<R>(H, c, dg);
+            const R g = ters_g<R>(H, c, dg);
+            zeta += fck * g;
             ++triplets;
+            if (own) {
+                // d c / d x_a = -[(v - c u)/r_q + (u - c v)/r_p]
+                const R cx = (vx - c * ux) * irq + (ux - c * vx) * irk;
+                const R cy = (vy - c * uy) * irq + (uy - c * vy) * irk;
+                const R cz = (vz - c * uz) * irq + (uz - c * vz) * irk;
+                const R t = fck * dg;
+                dx += -dfc * g * vx - t * cx;
+                dy += -dfc * g * vy - t * cy;
+                dz += -dfc * g * vz - t * cz;
+            }
         }
         R db;
         const R b = ters_b<R>(H, zeta, db);
@@ -536,21 +556,33 @@ __device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned lo
         o.b = dV;
         bond[q * cs] = o;
         E += R(0.5) * V;
+        if (own) {
+            fx += R(0.5) * dV * ux - o.a * dx;
+            fy += R(0.5) * dV * uy - o.a * dy;
+            fz += R(0.5) * dV * uz - o.a * dz;
+        }
+    }
+    if (own) {
+        V4<R> f;
+        f.x = fx;
+        f.y = fy;
+        f.z = fz;
+        f.w = R(0);
+        W.frc[a] = f;
     }
     return E;
 }
 
-// Tersoff pass 2: force on integrated atom i (list slot k) gathered from every
-// term of the energy that depends on its position: the bonds of i (radial
-// part and i as the centre of zeta_ib), the bonds (a, i) of its neighbours
-// (radial part and i as the partner in zeta_ai) and the bonds (a, b) in which
-// i is the third atom of zeta_ab.
+// Tersoff pass 2: the rest of the force on integrated atom i (list slot k),
+// gathered from the terms of its neighbours' bonds that depend on x_i: the
+// bonds (a, i) (radial part and i as the partner in zeta_ai) and the bonds
+// (a, b) in which i is the third atom of zeta_ab.  (The terms of i's own
+// bonds come from pass 1.)
 template <typename R, int TT>
 __device__ void ters_pass2(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& Fx, R& Fy, R& Fz)
 {
     const int m = W.nnb[k], cs = W.cap;
     const uint16_t* nb = W.nbr + k;   // entry q at [q * cs]
-    const V2<R>* bond_i = W.bond + k;
     const V4<R> pi = W.pos[i];
     R fx = R(0), fy = R(0), fz = R(0);
     for (int q = 0; q < m; ++q) {
@@ -563,39 +595,6 @@ __device__ void ters_pass2(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R
         const R ux = dx * ir, uy = dy * ir, uz = dz * ir;   // unit i -> a
         R dfa;
         const R fa = ters_fc<R>(H, ra, dfa);
-        const V2<R> bq = bond_i[q * cs];
-        fx += R(0.5) * bq.b * ux;
-        fy += R(0.5) * bq.b * uy;
-        fz += R(0.5) * bq.b * uz;
-        // i as the centre of zeta_ia
-        if (bq.a != R(0)) {
-            R gx = R(0), gy = R(0), gz = R(0);
-            for (int p = 0; p < m; ++p) {
-                if (p == q) continue;
-                const V4<R> pk = W.pos[nb[p * cs]];
-                const R ex = pk.x - pi.x, ey = pk.y - pi.y, ez = pk.z - pi.z;
-                const R r2k = ex * ex + ey * ey + ez * ez;
-                const R irk = Mth<R>::rsqrt(r2k);
-                R dfk;
-                const R fk = ters_fc<R>(H, r2k * irk, dfk);
-                if (fk <= R(0) && dfk == R(0)) continue;
-                const R vx = ex * irk, vy = ey * irk, vz = ez * irk;   // unit i -> k
-                const R c = ux * vx + uy * vy + uz * vz;
-                R dg;
-                const R g = ters_g<R>(H, c, dg);
-                // d c / d x_i = -[(v - c u)/r_a + (u - c v)/r_k]
-                const R cx = (vx - c * ux) * ir + (ux - c * vx) * irk;
-                const R cy = (vy - c * uy) * ir + (uy - c * vy) * irk;
-                const R cz = (vz - c * uz) * ir + (uz - c * vz) * irk;
-                const R t = fk * dg;
-                gx += -dfk * g * vx - t * cx;
-                gy += -dfk * g * vy - t * cy;
-                gz += -dfk * g * vz - t * cz;
-            }
-            fx -= bq.a * gx;
-            fy -= bq.a * gy;
-            fz -= bq.a * gz;
-        }
         // terms centred on the neighbour a
         const unsigned sa = W.need_map[a];
         if (sa >= REED_PENDING) continue;
@@ -696,14 +695,20 @@ __device__ __forceinline__ void atom_force(const DevParams& P, const HotParams<R
     V4<R> p = W.pos[i];
     const bool act = is_active(p);
     R fx = R(0), fy = R(0), fz = R(0);
+    if (TT == REED_TT_TERSOFF && act && k >= 0) {   // own-bond terms from pass 1
+        const V4<R> f1 = W.frc[i];
+        fx = f1.x;
+        fy = f1.y;
+        fz = f1.z;
+    }
     const R dx = p.x - ix, dy = p.y - iy, dz = p.z - iz;
     const R r2 = dx * dx + dy * dy + dz * dz;
     if (r2 < H.rc2) {
         R U, rw;
         const R g = ion_pair<R>(H, P.spline_on, P.rho_on, species_of(p), r2, U, rw);
-        fx = -g * dx;
-        fy = -g * dy;
-        fz = -g * dz;
+        fx -= g * dx;
+        fy -= g * dy;
+        fz -= g * dz;
         out.fx += g * dx;
         out.fy += g * dy;
         out.fz += g * dz;

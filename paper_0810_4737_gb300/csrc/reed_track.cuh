@@ -121,18 +121,17 @@ template <typename R, int TT> struct Win {
     unsigned* bin_count;  // scratch of the build, zero between builds
     uint16_t* slot_atom;  // list slot -> atom
     uint8_t* nnb;         // neighbours per slot
-    uint16_t* nbr;        // neighbour atoms, [neighbour][slot] (consecutive slots adjacent)
-    V2<R>* bond;          // [neighbour][slot]: {1/2 dV/db db/dzeta, dV/dr}
+    uint16_t* nbr;        // neighbour atoms per slot
+    V2<R>* bond;          // per slot and neighbour: {1/2 dV/db db/dzeta, dV/dr}
     V4<R>* xbar;          // adjoint of positions (adjoint runs)
     V4<R>* vbar;          // adjoint of velocities
-    int cap;              // list slots; nbr and bond are [neighbour][slot]
     // zero the bin counters (all threads; a barrier must follow)
     __device__ void clear_grid(const DevParams& P)
     {
         if (bin_count)
             for (int b = threadIdx.x; b < P.g_nbins; b += blockDim.x) bin_count[b] = 0u;
     }
-    __device__ Win(unsigned char* base, int na, int cap_, int adj = 0, int nbins = 0) : cap(cap_)
+    __device__ Win(unsigned char* base, int na, int cap, int adj = 0, int nbins = 0)
     {
         using L = Layout<R, TT>;
         S = reinterpret_cast<TrackShared<R>*>(base);
@@ -321,7 +320,7 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
                                       int& overflow)
 {
     const V4<R> pi = W.pos[i];
-    uint16_t* out = W.nbr + slot;   // entry q at out[q * W.cap]
+    uint16_t* out = W.nbr + (size_t)slot * maxnb(TT);
     int cnt = 0;
     const int nb = P.g_nb;
     const int bx = grid_axis<R>(P, H, pi.x), by = grid_axis<R>(P, H, pi.y), bz = grid_axis<R>(P, H, pi.z);
@@ -337,7 +336,7 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
                 const V4<R> pj = W.pos[j];
                 const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                 if (dx * dx + dy * dy + dz * dz < H.rlist2) {
-                    if (cnt < maxnb(TT)) out[(size_t)(cnt++) * W.cap] = (uint16_t)j;
+                    if (cnt < maxnb(TT)) out[cnt++] = (uint16_t)j;
                     else ++overflow;
                     if (TT == REED_TT_TERSOFF && !is_active(pj) && W.need_map[j] == REED_NO_SLOT)
                         W.need_map[j] = (uint16_t)REED_PENDING;
@@ -505,15 +504,15 @@ template <typename R, int TT>
 __device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned long long& triplets)
 {
     const int a = W.slot_atom[k];
-    const int m = W.nnb[k], cs = W.cap;
+    const int m = W.nnb[k];
     const bool own = k < W.S->active_count;
-    const uint16_t* nb = W.nbr + k;   // neighbour q at nb[q * cs]
-    V2<R>* bond = W.bond + k;
+    const uint16_t* nb = W.nbr + (size_t)k * REED_MAXNB;
+    V2<R>* bond = W.bond + (size_t)k * REED_MAXNB;
     const V4<R> pa = W.pos[a];
     R E = R(0);
     R fx = R(0), fy = R(0), fz = R(0);
     for (int q = 0; q < m; ++q) {
-        const V4<R> pq = W.pos[nb[q * cs]];
+        const V4<R> pq = W.pos[nb[q]];
         const R qx = pq.x - pa.x, qy = pq.y - pa.y, qz = pq.z - pa.z;
         const R r2q = qx * qx + qy * qy + qz * qz;
         const R irq = Mth<R>::rsqrt(r2q);
@@ -523,7 +522,7 @@ __device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned lo
         R dx = R(0), dy = R(0), dz = R(0);   // d zeta / d x_a
         for (int p = 0; p < m; ++p) {
             if (p == q) continue;
-            const V4<R> pk = W.pos[nb[p * cs]];
+            const V4<R> pk = W.pos[nb[p]];
             const R kx = pk.x - pa.x, ky = pk.y - pa.y, kz = pk.z - pa.z;
             const R r2k = kx * kx + ky * ky + kz * kz;
             const R irk = Mth<R>::rsqrt(r2k);
@@ -554,7 +553,7 @@ __device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned lo
         V2<R> o;
         o.a = R(0.5) * pfa * db;
         o.b = dV;
-        bond[q * cs] = o;
+        bond[q] = o;
         E += R(0.5) * V;
         if (own) {
             fx += R(0.5) * dV * ux - o.a * dx;
@@ -581,12 +580,12 @@ __device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned lo
 template <typename R, int TT>
 __device__ void ters_pass2(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& Fx, R& Fy, R& Fz)
 {
-    const int m = W.nnb[k], cs = W.cap;
-    const uint16_t* nb = W.nbr + k;   // entry q at [q * cs]
+    const int m = W.nnb[k];
+    const uint16_t* nb = W.nbr + (size_t)k * REED_MAXNB;
     const V4<R> pi = W.pos[i];
     R fx = R(0), fy = R(0), fz = R(0);
     for (int q = 0; q < m; ++q) {
-        const int a = nb[q * cs];
+        const int a = nb[q];
         const V4<R> pa = W.pos[a];
         const R dx = pa.x - pi.x, dy = pa.y - pi.y, dz = pa.z - pi.z;
         const R r2 = dx * dx + dy * dy + dz * dz;
@@ -599,14 +598,14 @@ __device__ void ters_pass2(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R
         const unsigned sa = W.need_map[a];
         if (sa >= REED_PENDING) continue;
         const int ma = W.nnb[sa];
-        const uint16_t* nba = W.nbr + sa;
-        const V2<R>* bond_a = W.bond + sa;
+        const uint16_t* nba = W.nbr + (size_t)sa * REED_MAXNB;
+        const V2<R>* bond_a = W.bond + (size_t)sa * REED_MAXNB;
         const R vx = -ux, vy = -uy, vz = -uz;   // unit a -> i
         R ax = R(0), ay = R(0), az = R(0);      // d zeta_ai / d x_i
         R pre_ai = R(0), dV_ai = R(0);
         for (int p = 0; p < ma; ++p) {
-            const int b = nba[p * cs];
-            const V2<R> bab = bond_a[p * cs];
+            const int b = nba[p];
+            const V2<R> bab = bond_a[p];
             if (b == i) {
                 pre_ai = bab.a;
                 dV_ai = bab.b;
@@ -652,11 +651,10 @@ __device__ R pair_force(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& F
     const int m = W.nnb[k];
     const V4<R> pi = W.pos[i];
     const int si = species_of(pi);
-    const uint16_t* nb = W.nbr + k;
-    const int cs = W.cap;
+    const uint16_t* nb = W.nbr + (size_t)k * maxnb(TT);
     R E = R(0);
     for (int q = 0; q < m; ++q) {
-        const V4<R> pj = W.pos[nb[q * cs]];
+        const V4<R> pj = W.pos[nb[q]];
         R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
         R r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= H.b_rc2) continue;

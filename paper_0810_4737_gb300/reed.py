@@ -449,7 +449,7 @@ class Reed:
     def autotune(self, n_trial, seed=None, precision=PREC_MIXED, **kw):
         """Time the launch configurations on n_trial primaries and keep the
         fastest for later runs; returns [(threads, ctas_per_sm, ion-steps/s)]."""
-        w = self.w
+        w = dict(self.w, step_cap=kw.pop("step_cap", self.w["step_cap"]))
         o = run_opts(w, precision=precision, **kw)
         ion = w["ion"]
         tab = (reed_tune_entry * 16)()

@@ -134,6 +134,25 @@ def cpu_baseline(w, n_ions, threads, step_cap):
     return r["steps"] / dt, r["steps"], dt
 
 
+def oracle_parity(R, n):
+    """Mean, straggle and two-sample KS p of the range profile of each GPU
+    form against the oracle on the same primaries."""
+    from oracle import oracle as O
+    from paper_0810_4737_gb300.workloads import workload
+    w = workload("b1kev_si_0k_zbl")
+    ref = O.run(O.params(w), n, seed=1, threads=os.cpu_count() or 1)["records"]
+    zo = ref["z"][ref["status"] == 1]
+    out = {"workload": w["name"], "ions": n, "oracle_mean_A": float(np.mean(zo)), "oracle_straggle_A": float(np.std(zo))}
+    for name, prec in (("mixed", R.PREC_MIXED), ("fp64", R.PREC_FP64)):
+        with R.Reed(w) as c:
+            c.run(n_ions=n, seed=1, precision=prec)
+            rec = c.records()
+        z = rec["z"][rec["status"] == 1]
+        out[name] = {"mean_rel_err": float(np.mean(z) / np.mean(zo) - 1), "straggle_rel_err": float(np.std(z) / np.std(zo) - 1),
+                     "ks_p": _ks(z, zo)}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -287,6 +306,11 @@ def main():
                 "mixed_same_sample": s32["steps"] / (s32["kernel_ms"] * 1e-3), "sample_ions": m,
                 "ks_p_mixed_vs_fp64": _ks(z32, z64),
                 "mean_depth_A": [float(np.mean(z32)) if len(z32) else None, float(np.mean(z64)) if len(z64) else None]}
+    # ---- per-profile error of both GPU forms against the oracle on the small
+    # workload (4096 B ions at 1 keV, 0 K; full tracks are cheap on the CPU there)
+    parity = None
+    if rank == 0 and not args.no_cpu:
+        parity = oracle_parity(R, 4096)
     # ---- CPU oracle on the host cores (bounded sample)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -321,6 +345,7 @@ def main():
                          "kernel_ms_per_launch": sum(kernel_ms) / len(kernel_ms)},
             "peaks": peaks,
             "fp64_path": fp64,
+            "oracle_parity": parity,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "stats": {k: st[k] for k in ("primaries", "tracks", "steps", "pair_evals", "bond_evals", "triplets",

@@ -38,7 +38,7 @@ SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) per ion-step of the stepper kernel from the ncu
 # capture summarised in profiles/reed_track_kernel_tersoff_as10kev.md (None
 # when the kernel has changed since).
-TRAFFIC_PER_ION_STEP = None
+TRAFFIC_PER_ION_STEP = 0.254
 
 
 def _ion_name(w):

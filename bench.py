@@ -35,10 +35,11 @@ WORKLOAD = "as10kev_si_300k_tersoff"
 # 35 ops, integrated atom update 12 FMA = 24 ops, Tersoff bond-angle triplet 60 ops.
 OPS_PAIR, OPS_MOVE, OPS_TRIPLET = 35, 24, 60
 SMS, FP32_LANES = 152, 128
-# DRAM bytes (read + write) per ion-step of the stepper kernel from the ncu
-# capture summarised in profiles/reed_track_kernel_tersoff_as10kev.md (None
-# when the kernel has changed since).
-TRAFFIC_PER_ION_STEP = 0.254
+# DRAM bytes (read + write) of one bench launch of the stepper kernel (4096
+# ions), from the one-pass ncu capture of that launch summarised in
+# profiles/reed_track_kernel_tersoff_as10kev.md (None when the kernel has
+# changed since).
+TRAFFIC_PER_LAUNCH = 400_130
 
 
 def _ion_name(w):
@@ -337,8 +338,7 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
-                         "frac": achieved / peaks["fp32_tflops"], "traffic": TRAFFIC_PER_ION_STEP * steps_done / ws
-                         / args.steps if TRAFFIC_PER_ION_STEP is not None else None,
+                         "frac": achieved / peaks["fp32_tflops"], "traffic": TRAFFIC_PER_LAUNCH if w["name"] == WORKLOAD and n == 4096 else None,
                          "peak_source": "measured FP32 FMA stream (reed_peaks, burst) at %.0f MHz; derived "
                                         "152 SM x 128 lanes x 2 x 2070 MHz = %.1f" % (peaks["sm_mhz"], derived),
                          "kernel": "reed_track_kernel<float, %s>" % w["tt"].upper(),

@@ -150,8 +150,23 @@ def oracle_parity(R, n):
             rec = c.records()
         z = rec["z"][rec["status"] == 1]
         out[name] = {"mean_rel_err": float(np.mean(z) / np.mean(zo) - 1), "straggle_rel_err": float(np.std(z) / np.std(zo) - 1),
-                     "ks_p": _ks(z, zo)}
+                     "ks_p": _ks(z, zo),
+                     # sampling error of the two estimates (trajectories are chaotic, so
+                     # the two samples are effectively independent)
+                     "mean_rel_se": float(np.hypot(_se_mean(z), _se_mean(zo))),
+                     "straggle_rel_se": float(np.hypot(_se_std(z), _se_std(zo)))}
     return out
+
+
+def _se_mean(z):
+    return np.std(z) / np.sqrt(len(z)) / np.mean(z)
+
+
+def _se_std(z):
+    # relative standard error of the sample standard deviation: sqrt((kurtosis - 1) / (4 n))
+    d = z - np.mean(z)
+    kurt = np.mean(d ** 4) / np.mean(d ** 2) ** 2
+    return np.sqrt(max(kurt - 1.0, 0.0) / (4 * len(z)))
 
 
 def run_reference(args):

@@ -318,7 +318,11 @@ def main():
             r32 = c32.records()
         z64 = r64["z"][r64["status"] == R.STOPPED]
         z32 = r32["z"][r32["status"] == R.STOPPED]
+        f64ops = OPS_PAIR * s64["pair_evals"] + OPS_MOVE * s64["atom_updates"] + OPS_TRIPLET * s64["triplets"]
+        a64 = f64ops / (s64["kernel_ms"] * 1e-3) / 1e12
         fp64 = {"value": s64["steps"] / (s64["kernel_ms"] * 1e-3), "unit": "ion-steps/s",
+                "roofline": {"bound": "fp64", "achieved": a64, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                             "frac": a64 / peaks["fp64_tflops"], "peak_source": "measured FP64 FMA stream (reed_peaks)"},
                 "mixed_same_sample": s32["steps"] / (s32["kernel_ms"] * 1e-3), "sample_ions": m,
                 "ks_p_mixed_vs_fp64": _ks(z32, z64),
                 "mean_depth_A": [float(np.mean(z32)) if len(z32) else None, float(np.mean(z64)) if len(z64) else None]}

@@ -205,3 +205,34 @@ def test_autotune_keeps_the_fastest_and_results_do_not_change(R):
         plain = ctx.records()
     a, b = np.sort(tuned, order="id"), np.sort(plain, order="id")
     assert np.array_equal(a, b)
+
+
+def test_rare_event_workload_full_size(R):
+    """65536 B ions at 50 keV with 12 cloning depths (weights 2^-k): exact
+    weight accounting, no lost clone, and the same weighted range
+    distribution as the unenhanced run of the same primaries, resolved over
+    many more decades."""
+    w = workload("b50kev_si_300k_reed")
+    n = int(w["n_ions"])
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n, seed=0)
+        st = ctx.stats()
+        rec = ctx.records()
+        bins, extra = ctx.profile()
+    assert st["primaries"] == n and st["dropped_clones"] == 0 and st["failed"] == 0
+    assert st["tracks"] == n + st["clones"] == len(rec) and st["clones"] > n
+    wts = np.ldexp(1.0, -rec["level"].astype(int))
+    assert np.sum(wts) == n
+    assert bins.sum() + extra.sum() + st["w_trunc"] == n
+    assert len(np.unique(rec["id"])) == len(rec)
+    with R.Reed(dict(w, thresholds=[])) as ctx:
+        ctx.run(n_ions=n, seed=0)
+        plain = ctx.records()
+        pbins, _ = ctx.profile()
+    sg, sp = rec["status"] == 1, plain["status"] == 1
+    D, pval = _wks(rec["z"][sg], wts[sg], plain["z"][sp], np.ones(int(sp.sum())))
+    assert pval > 0.01, (D, pval)
+    # the enhanced profile reaches far smaller weights than one primary's
+    tot = bins.sum()
+    assert bins[bins > 0].min() / tot < 1e-7 < 1.0 / n
+    assert np.count_nonzero(bins) > np.count_nonzero(pbins)

@@ -206,6 +206,8 @@ typedef struct {
     double w_stopped, w_back, w_trunc;   /* weights */
     double kernel_ms;        /* device time of the last reed_run */
     int32_t threads_per_track, ctas_per_sm, grid, smem_bytes;  /* last launch */
+    int64_t splits[16];      /* clones made on first passing cloning depth k+1 (the
+                                paper's per-depth split statistics, Sec. 3) */
 } reed_stats_t;
 
 typedef struct reed_ctx reed_ctx;

@@ -57,6 +57,7 @@ struct reed_ctx {
     double bin_w = 0.0;
     double* d_hist = nullptr;
     unsigned long long* d_counters = nullptr;
+    unsigned long long* d_splits = nullptr;   // clones per cloning level
     double* d_wsum = nullptr;
     unsigned long long* d_next = nullptr;
     int* d_status = nullptr;
@@ -542,6 +543,7 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     ctx->smem_optin = (size_t)optin;
     if (cudaMalloc((void**)&ctx->d_counters, sizeof(unsigned long long) * REED_NCOUNT) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_splits, sizeof(unsigned long long) * REED_MAX_THR) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_wsum, sizeof(double) * 4) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_next, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_status, sizeof(int)) != cudaSuccess ||
@@ -554,6 +556,7 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
         return fail(nullptr, REED_E_NOMEM, "device allocation failed");
     }
     cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT);
+    cudaMemset(ctx->d_splits, 0, sizeof(unsigned long long) * REED_MAX_THR);
     cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4);
     cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long));
     {   // no cloning depth until one is set
@@ -684,6 +687,7 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     }
     B.hist = ctx->d_hist;
     B.counters = ctx->d_counters;
+    B.splits = ctx->d_splits;
     B.wsum = ctx->d_wsum;
     B.next = ctx->d_next;
     B.records = ctx->d_records;
@@ -833,9 +837,10 @@ int reed_range_profile(reed_ctx* ctx, double* bins_out, int n_bins, double* extr
 int reed_stats(reed_ctx* ctx, reed_stats_t* out)
 {
     if (!ctx || !out) return REED_E_ARG;
-    unsigned long long c[REED_NCOUNT];
+    unsigned long long c[REED_NCOUNT], sp[REED_MAX_THR];
     double w[4];
     CK(cudaMemcpy(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(sp, ctx->d_splits, sizeof(sp), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(w, ctx->d_wsum, sizeof(w), cudaMemcpyDeviceToHost));
     std::memset(out, 0, sizeof(*out));
     out->primaries = (int64_t)c[C_PRIMARIES];
@@ -852,6 +857,7 @@ int reed_stats(reed_ctx* ctx, reed_stats_t* out)
     out->triplets = (int64_t)c[C_TRIPLETS];
     out->atom_updates = (int64_t)c[C_MOVED];
     for (int k = 0; k < REED_NPHASE; ++k) out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
+    for (int k = 0; k < REED_MAX_THR; ++k) out->splits[k] = (int64_t)sp[k];
     out->failed = (int64_t)c[C_FAILED];
     out->stopped = (int64_t)c[C_STOP];
     out->backscattered = (int64_t)c[C_BACK];
@@ -1038,6 +1044,7 @@ int reed_reset(reed_ctx* ctx)
     ctx->d_grads = nullptr;
     ctx->grads_cap = 0;
     CK(cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT));
+    CK(cudaMemset(ctx->d_splits, 0, sizeof(unsigned long long) * REED_MAX_THR));
     CK(cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4));
     CK(cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long)));
     return REED_OK;
@@ -1048,7 +1055,7 @@ const char* reed_last_error(reed_ctx* ctx) { return ctx ? ctx->err.c_str() : g_i
 void reed_destroy(reed_ctx* ctx)
 {
     if (!ctx) return;
-    void* ptrs[] = {ctx->d_hist, ctx->d_counters, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
+    void* ptrs[] = {ctx->d_hist, ctx->d_counters, ctx->d_splits, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
                     ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch,
                     ctx->d_thr, ctx->d_thr_hist, ctx->d_finished, ctx->d_damage, ctx->d_grads,
                     ctx->d_adj, ctx->d_kde};
@@ -1435,6 +1442,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     B.status = reinterpret_cast<int*>(base + 768);
     B.record_count = reinterpret_cast<unsigned long long*>(base + 1024);
     B.finished = reinterpret_cast<unsigned long long*>(base + 1280);
+    B.splits = reinterpret_cast<unsigned long long*>(base + 1536);
     B.thr = nullptr;
     B.damage = nullptr;
     P.stop_after = o.target_tracks;
@@ -1476,6 +1484,9 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
         stats_out->triplets = (int64_t)c[C_TRIPLETS];
         stats_out->atom_updates = (int64_t)c[C_MOVED];
         for (int k = 0; k < REED_NPHASE; ++k) stats_out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
+        unsigned long long sp[REED_MAX_THR];
+        CK(cudaMemcpy(sp, B.splits, sizeof(sp), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < REED_MAX_THR; ++k) stats_out->splits[k] = (int64_t)sp[k];
         stats_out->w_stopped = w[W_STOPPED];
         stats_out->w_back = w[W_BACK];
         stats_out->w_trunc = w[W_TRUNC];

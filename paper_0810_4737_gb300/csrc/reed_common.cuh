@@ -117,6 +117,7 @@ struct DevParams {
 struct DevBuf {
     double* hist;                   // nbins + 3 (under, over, back)
     unsigned long long* counters;   // REED_NCOUNT
+    unsigned long long* splits;     // clones made at each cloning level (REED_MAX_THR), may be null
     double* wsum;                   // W_*
     unsigned long long* next;       // primary queue head
     reed_track_record* records;

@@ -1297,6 +1297,7 @@ __global__ void __launch_bounds__(256, (track_min_ctas<R, TT, ADJ>())) reed_trac
                     C.key = track_key(P.seed, C.id);
                     *reinterpret_cast<IonState<R>*>(rec) = C;
                     ++c_clone;
+                    if (B.splits) atomicAdd(&B.splits[min(I.level, REED_MAX_THR) - 1], 1ull);
                 }
                 copy_window<R, TT>(P, W, rec, true);
                 __syncthreads();

@@ -129,6 +129,8 @@ def test_cloning_conserves_weight_and_statistics(R, O):
     assert bins.sum() + extra.sum() + st["w_trunc"] == n
     assert st["tracks"] == n + st["clones"] == len(rec)
     assert st["dropped_clones"] == 0
+    # per-depth split statistics: every clone counted once, at a used depth
+    assert sum(st["splits"]) == st["clones"] and not any(st["splits"][6:])
     assert len(np.unique(rec["id"])) == len(rec)
     # every lineage has exactly one primary record
     assert np.sum(rec["id"] == rec["primary"]) == n

@@ -175,6 +175,13 @@ typedef struct {
      * nl_skin; a list is rebuilt after a window move and when the two longest
      * atom paths since the last build add up to more than nl_skin.  0 = 0.3 A. */
     double nl_skin;
+    /* Energy term of the adaptive step (the paper's step rule in terms of the
+     * kinetic and collisional energy, Sec. 2): when > 0, also
+     * dt <= de_max / P with P the largest |F . v| over the ion and the
+     * integrated atoms at the start of the step (conservative forces), i.e. no
+     * particle's kinetic energy changes by much more than de_max (eV) in one
+     * step.  0 = off. */
+    double de_max;
 } reed_run_opts;
 
 /* Per-track result: the depth and weight of one finished track (Sec. 3, result messages). */

@@ -59,6 +59,7 @@ class Params(C.Structure):
         ("nthr", C.c_int), ("thr", C.c_double * 16),
         ("nbins", C.c_int), ("bin_w", C.c_double),
         ("dn", C.c_int), ("dvox", C.c_double), ("dmin", C.c_double),
+        ("de_max", C.c_double),
     ]
 
 
@@ -187,6 +188,7 @@ def params(w: dict, screening: int = 1) -> Params:
         p.thr[i] = d
     p.nbins, p.bin_w = int(w["n_bins"]), float(w["bin_w"])
     p.dn, p.dvox, p.dmin = int(w.get("damage_n", 0)), float(w.get("damage_voxel", 10.0)), float(w.get("damage_min", 0.1))
+    p.de_max = float(w.get("de_max", 0.0))
     return p
 
 

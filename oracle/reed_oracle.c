@@ -96,6 +96,8 @@ typedef struct {
      * (-dn dvox / 2, -dn dvox / 2, 0); atoms with KE > dmin deposit w KE */
     int dn;
     double dvox, dmin;
+    /* energy term of the adaptive step (eV per step; 0 = off) */
+    double de_max;
 } o_params;
 
 typedef struct {
@@ -707,7 +709,10 @@ double o_forces(const o_params* P, const double* xi, int with_ion, int n, const 
 /* Integrator (Sec. 2: Verlet with adaptive time step).                     */
 /* reading: dt = min(dt_max, dx_max / v_max), v_max over the ion and the     */
 /* integrated atoms; kick-drift-kick with the drag evaluated at the velocity */
-/* available at each half kick.                                             */
+/* available at each half kick.  Optional energy term (the paper's step in  */
+/* terms of kinetic and collisional energy, reading): dt <= de_max / P, P   */
+/* the largest |F . v| (conservative force, velocity) over the ion and the  */
+/* integrated atoms at the start of the step.                               */
 /* ------------------------------------------------------------------------ */
 static void o_drag(const o_params* P, double gam, double rho0, const o_ion* I, const double* v,
                    const double* x, double rho, double F[3])
@@ -734,6 +739,16 @@ static double o_pick_dt(const o_params* P, const o_ion* I, const o_win* W)
     double vmax = sqrt(v2);
     double dt = P->dt_max;
     if (vmax * dt > P->dx_max) dt = P->dx_max / vmax;
+    if (P->de_max > 0.0) {
+        double pw = fabs(I->f[0] * I->v[0] + I->f[1] * I->v[1] + I->f[2] * I->v[2]);
+        for (int j = 0; j < W->n; ++j) {
+            if (!W->act[j]) continue;
+            double q = fabs(W->f[3 * j] * W->v[3 * j] + W->f[3 * j + 1] * W->v[3 * j + 1] +
+                            W->f[3 * j + 2] * W->v[3 * j + 2]);
+            if (q > pw) pw = q;
+        }
+        if (pw * dt > P->de_max) dt = P->de_max / pw;
+    }
     return dt;
 }
 

@@ -266,7 +266,7 @@ __device__ void replay_step(const DevParams& P, const HotParams<R>& H, Win<R, TT
     reduce_partials<R, TT>(W, q);
     __syncthreads();
     if (threadIdx.x == 0) {
-        R red[8];
+        R red[REED_NRED];
         gather_partials<R, TT>(W, red);
         IonState<R>& I = S->ion;
         for (int d = 0; d < 3; ++d) I.f[d] = red[d];

@@ -170,6 +170,7 @@ template <typename T> void fill_hot(HotParams<T>& h, const DevParams& P, const r
     double cut = P.tt == REED_TT_BUCKINGHAM ? q.buck_cut[1] : R + D;
     h.rlist2 = (T)((cut + skin) * (cut + skin));
     h.skin = (T)skin;
+    h.de_max = (T)P.de_max;
     h.g_lo = (T)(-P.half_n * P.a);
     h.g_inv = (T)(P.g_nb / (P.n * P.a));
     // Buckingham
@@ -336,6 +337,7 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.dvox = o.damage_voxel > 0 ? o.damage_voxel : 10.0;
     P.dhalf = 0.5 * P.dn * P.dvox;
     P.dmin = o.damage_min;
+    P.de_max = o.de_max > 0.0 ? o.de_max : 0.0;
     const double skin = o.nl_skin > 0.0 ? o.nl_skin : kSkin;
     // neighbour-search grid over the window: bins no narrower than the list
     // radius (with a margin for rounding), at most 10 per axis

@@ -30,6 +30,7 @@ __host__ __device__ constexpr int maxnb(int tt) { return tt == REED_TT_BUCKINGHA
 #define REED_W_EMPTY (-1)
 
 enum { REED_NCOUNT = 24 };
+enum { REED_NRED = 9 };   // per-warp partial sums of a force pass
 // cycle counters of the step phases (thread 0 of every CTA, summed)
 enum { PH_ION = 0, PH_MOVE, PH_BUILD, PH_PASS1, PH_FORCE, PH_ADMIN, REED_NPHASE };
 #define C_PHASE0 C_SPARE
@@ -52,6 +53,7 @@ template <typename R> struct HotParams {
     R tA, tB, tl1, tl2, tbn, tn, tmhn, tc2, td2, th, tRmD, tcut, tq, tdq, tR, tc2d2;
     R t_blo, t_binvw, t_zk, t_zia, rlist2, skin;
     R g_lo, g_inv;   // neighbour-search grid: low corner (anchor frame) and bins per A
+    R de_max;        // energy term of the adaptive step (0 = off)
     // Buckingham
     R bA[3], brho_inv[3], bC[3], b_lo, b_binvw, b_rt, b_rinvw, b_rc2, b_zk[3], b_zia[3];
     // ion step
@@ -88,7 +90,7 @@ struct DevParams {
     double gamma, s_loc, rho0_inv, lam_inv;
     int rho_on;
     // integrator (Sec. 2, Fig. "dt_E")
-    double dt_max, dx_max, e_stop;
+    double dt_max, dx_max, e_stop, de_max;
     long long step_cap;
     // beam
     double v0, tilt, rot_lo, rot_span, cos_tmax;

@@ -42,6 +42,7 @@ template <typename R> struct IonState {
     double t, e_elec;     // time (tau), energy removed by the drag (eV)
     R v[3], f[3];         // velocity (A/tau), conservative force (eV/A)
     R rho, vmax2;         // local density at x; fastest atom's speed^2
+    R pmax;               // largest |F . v| over the integrated atoms (energy term of dt)
     long long steps;
     unsigned long long id, primary, key;
     int A[3];
@@ -66,7 +67,7 @@ template <typename R> struct TrackShared {
     int need_count, active_count;
     int scan[2][REED_MAX_WARPS];
     long long pidx;
-    R red[REED_MAX_WARPS][8];
+    R red[REED_MAX_WARPS][REED_NRED];
     R path2[REED_MAX_WARPS][2];   // per warp: the two longest atom paths since the list build
 };
 
@@ -672,6 +673,7 @@ __device__ R pair_force(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& F
 template <typename R> struct Partial {
     R fx, fy, fz, rho, vmax2, epot;
     int pairs, bonds;
+    R pmax;
 };
 
 // Per-thread work counters (algorithmic units of a step, see stats).
@@ -742,6 +744,7 @@ __device__ __forceinline__ void atom_force(const DevParams& P, const HotParams<R
         v.z += kk * fz;
         W.vel[i] = v;
         out.vmax2 = max(out.vmax2, v.x * v.x + v.y * v.y + v.z * v.z);
+        if (H.de_max > R(0)) out.pmax = max(out.pmax, fabs(fx * v.x + fy * v.y + fz * v.z));
     }
 }
 
@@ -774,29 +777,31 @@ __device__ __forceinline__ void reduce_partials(Win<R, TT>& W, Partial<R>& q)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     R fx = warp_sum(q.fx), fy = warp_sum(q.fy), fz = warp_sum(q.fz), rho = warp_sum(q.rho);
-    R vm = warp_max(q.vmax2), ep = warp_sum(q.epot);
+    R vm = warp_max(q.vmax2), ep = warp_sum(q.epot), pm = warp_max(q.pmax);
     int pr = warp_sum(q.pairs), bd = warp_sum(q.bonds);
     if (lane == 0) {
         R* row = W.S->red[wid];
         row[0] = fx; row[1] = fy; row[2] = fz; row[3] = rho; row[4] = vm; row[5] = ep;
-        row[6] = R(pr); row[7] = R(bd);
+        row[6] = R(pr); row[7] = R(bd); row[8] = pm;
     }
 }
 
-// Sum the per-warp partials (thread 0), fixed order.
+// Sum the per-warp partials (thread 0), fixed order; rows 4 and 8 are maxima.
 template <typename R, int TT>
-__device__ __forceinline__ void gather_partials(Win<R, TT>& W, R out[8])
+__device__ __forceinline__ void gather_partials(Win<R, TT>& W, R out[REED_NRED])
 {
     const int nw = (blockDim.x + 31) >> 5;
-    R acc[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    R acc[REED_NRED];
+#pragma unroll
+    for (int c = 0; c < REED_NRED; ++c) acc[c] = R(0);
     for (int w = 0; w < nw; ++w) {
         const R* row = W.S->red[w];
-        for (int c = 0; c < 8; ++c) {
-            if (c == 4) acc[4] = max(acc[4], row[4]);
+        for (int c = 0; c < REED_NRED; ++c) {
+            if (c == 4 || c == 8) acc[c] = max(acc[c], row[c]);
             else acc[c] += row[c];
         }
     }
-    for (int c = 0; c < 8; ++c) out[c] = acc[c];
+    for (int c = 0; c < REED_NRED; ++c) out[c] = acc[c];
 }
 
 // Depth bin tally and per-track record of a finished track (Sec. 3: result
@@ -873,6 +878,7 @@ template <typename R> __device__ void launch_primary(const DevParams& P, IonStat
     I.f[0] = I.f[1] = I.f[2] = R(0);
     I.rho = R(0);
     I.vmax2 = R(0);
+    I.pmax = R(0);
     I.t = 0.0;
     I.e_elec = 0.0;
     I.steps = 0;
@@ -911,6 +917,10 @@ template <typename R> __device__ void ion_prologue(const DevParams& P, const Hot
     const R vmax = sqrt(max(v2, I.vmax2));
     R dt = H.dt_max;
     if (vmax * dt > H.dx_max) dt = H.dx_max / vmax;
+    if (H.de_max > R(0)) {   // energy term: |dE_kin| <= de_max per step for every particle
+        const R pw = max(fabs(I.f[0] * I.v[0] + I.f[1] * I.v[1] + I.f[2] * I.v[2]), I.pmax);
+        if (pw * dt > H.de_max) dt = H.de_max / pw;
+    }
     const R kd = drag_k<R>(H, S);
     S->on1 = S->rel[2] >= S->zsurf;
     const R h = R(0.5) * dt * H.invM1;
@@ -941,7 +951,7 @@ template <typename R> __device__ void ion_prologue(const DevParams& P, const Hot
 // Epilogue (thread 0): ion second half kick, end and cloning checks.
 // Returns EV_NONE / EV_END / EV_CLONE; sets S->status and S->nclone.
 template <typename R>
-__device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShared<R>* S, const R red[8])
+__device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShared<R>* S, const R red[REED_NRED])
 {
     IonState<R>& I = S->ion;
     const R dt = S->dt;
@@ -950,6 +960,7 @@ __device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShar
     I.f[2] = red[2];
     I.rho = red[3];
     I.vmax2 = red[4];
+    I.pmax = red[8];
     const R kd = drag_k<R>(H, S);
     S->on2 = S->rel[2] >= S->zsurf;
     const R h = R(0.5) * dt * H.invM1;
@@ -1020,7 +1031,7 @@ __device__ void initial_forces(const DevParams& P, const HotParams<R>& H, Win<R,
     reduce_partials<R, TT>(W, q);
     __syncthreads();
     if (threadIdx.x == 0) {
-        R red[8];
+        R red[REED_NRED];
         gather_partials<R, TT>(W, red);
         IonState<R>& I = W.S->ion;
         I.f[0] = red[0];
@@ -1228,7 +1239,7 @@ __global__ void __launch_bounds__(256, (track_min_ctas<R, TT, ADJ>())) reed_trac
             __syncthreads();
             lap(PH_FORCE);
             if (tid == 0) {
-                R red[8];
+                R red[REED_NRED];
                 gather_partials<R, TT>(W, red);
                 c_pairs += (unsigned long long)red[6];
                 c_bonds += (unsigned long long)red[7];

@@ -72,6 +72,7 @@ _BASE = {
     "lam_loc": 0.5,
     "dt_max_fs": 0.1,
     "dx_max": 0.05,
+    "de_max": 0.0,          # eV per step, energy term of the adaptive step (0 = off)
     "e_stop": 5.0,
     "step_cap": 2_000_000,
     "beam_mode": "fixed",

@@ -64,6 +64,16 @@ def test_first_50_steps_thermal(R, O, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_first_steps_with_the_energy_term(R, O, prec):
+    # the optional energy term of the adaptive step (dt <= de_max / max |F.v|)
+    w = workload("b1kev_si_0k_zbl", sigma=0.076, rot=(0.0, 45.0), de_max=1.0)
+    _trace_check(R, O, w, 16, 50, prec, 1e-4)
+    _trace_check(R, O, w, 16, 400, prec, 1e-4 if prec == 1 else 1e-2)
+    wt = workload("as10kev_si_300k_tersoff", de_max=2.0)
+    _trace_check(R, O, wt, 2, 50, prec, 1e-4)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_first_50_steps_tersoff(R, O, prec):
     w = workload("as10kev_si_300k_tersoff")
     _trace_check(R, O, w, 4, 50, prec, 1e-4)

@@ -239,3 +239,32 @@ def test_damage_map_totals(O):
     zmax = r["records"]["z"].max()
     iz = np.nonzero(d.sum(axis=(0, 1)))[0]
     assert iz.max() * 5.0 <= zmax + 3 * 5.431 + 5.0
+
+
+def test_energy_term_of_the_time_step(O):
+    """With the optional energy term on (and stopping off, so only the
+    conservative force changes the ion's energy), no step changes the ion's
+    kinetic energy by much more than de_max, while the plain rule does in hard
+    collisions; the range distribution does not move."""
+    w0 = workload("b1kev_si_0k_zbl", s_e=0.0, sigma=0.076, rot=(0.0, 45.0))
+    w1 = dict(w0, de_max=1.0)
+    M = B11["M"]
+    worst0, worst1, steps0, steps1 = 0.0, 0.0, 0, 0
+    for tid in range(6):
+        for w in (w0, w1):
+            tr, _ = O.trace(O.params(w), 0, tid, 20000)
+            E = 0.5 * M * np.sum(tr[:, 4:7] ** 2, axis=1)
+            dE = np.max(np.abs(np.diff(E)))
+            if w is w0:
+                worst0, steps0 = max(worst0, dE), steps0 + len(tr)
+            else:
+                worst1, steps1 = max(worst1, dE), steps1 + len(tr)
+    assert worst0 > 20.0           # the plain rule takes big bites in collisions
+    # |dE| ~ |F.v| dt <= de_max to first order; the power can grow within a
+    # step as the ion closes in, so allow a small multiple
+    assert worst1 < 2.5 * 1.0 and worst0 > 10 * worst1
+    assert steps1 > steps0
+    r0 = O.run(O.params(w0), 256, seed=2)["records"]
+    r1 = O.run(O.params(w1), 256, seed=2)["records"]
+    z0, z1 = r0["z"][r0["status"] == 1], r1["z"][r1["status"] == 1]
+    assert abs(np.mean(z1) / np.mean(z0) - 1) < 0.06

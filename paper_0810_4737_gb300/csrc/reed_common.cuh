@@ -268,6 +268,30 @@ __device__ __forceinline__ void box_muller3(const uint32_t w[4], double g[3])
     g[2] = r2 * c2;
 }
 
+// The same three normals in FP32 (the mixed form's thermal offsets; FP64
+// transcendentals are slow on this part).  -ln u is taken from 1 - u when u
+// is near 1 so that small radii keep their relative accuracy.
+__device__ __forceinline__ float neg_log_unit(uint32_t w)
+{
+    if (w >= 0x80000000u) {
+        const float e = ((float)(0xFFFFFFFFu - w) + 0.5f) * 2.3283064365386963e-10f;   // 1 - u
+        return -log1pf(-e);
+    }
+    return -logf(((float)w + 0.5f) * 2.3283064365386963e-10f);
+}
+
+__device__ __forceinline__ void box_muller3f(const uint32_t w[4], float g[3])
+{
+    const float r1 = sqrtf(2.0f * neg_log_unit(w[0]));
+    const float r2 = sqrtf(2.0f * neg_log_unit(w[2]));
+    float s1, c1;
+    sincospif(2.0f * (((float)w[1] + 0.5f) * 2.3283064365386963e-10f), &s1, &c1);
+    const float c2 = cospif(2.0f * (((float)w[3] + 0.5f) * 2.3283064365386963e-10f));
+    g[0] = r1 * c1;
+    g[1] = r1 * s1;
+    g[2] = r2 * c2;
+}
+
 // ---------------------------------------------------------------------------
 // Warp reductions (fixed butterfly order: results are reproducible).
 // ---------------------------------------------------------------------------

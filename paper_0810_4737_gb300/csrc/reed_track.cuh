@@ -220,7 +220,15 @@ __device__ void make_atom(const DevParams& P, uint64_t key, int i, const int A[3
     if (P.sigma > 0.0) {
         uint32_t w[4];
         draw4(key, c[0], c[1], c[2], ((uint32_t)b << 4) | REED_TAG_CELL, w);
-        box_muller3(w, g);
+        if constexpr (sizeof(R) == 4) {
+            float gf[3];
+            box_muller3f(w, gf);
+            g[0] = gf[0];
+            g[1] = gf[1];
+            g[2] = gf[2];
+        } else {
+            box_muller3(w, g);
+        }
     }
     p.x = R(((double)(c[0] - A[0]) + P.bas[b][0]) * P.a + P.sigma * g[0]);
     p.y = R(((double)(c[1] - A[1]) + P.bas[b][1]) * P.a + P.sigma * g[1]);

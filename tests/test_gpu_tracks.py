@@ -220,14 +220,16 @@ def test_autotune_keeps_the_fastest_and_results_do_not_change(R):
 
 
 def test_rare_event_workload_full_size(R):
-    """65536 B ions at 50 keV with 12 cloning depths (weights 2^-k): exact
-    weight accounting, no lost clone, and the same weighted range
-    distribution as the unenhanced run of the same primaries, resolved over
-    many more decades."""
+    """65536 B ions at 50 keV with 12 cloning depths (weights 2^-k) placed
+    adaptively (50 unenhanced primaries, then epochs of 4096 with d_k =
+    S^-1(2^-k); fixed depths below the mean range would double every track at
+    each of them): exact weight accounting, no lost clone, and the same
+    weighted range distribution as the unenhanced run of the same primaries,
+    resolved over many more decades."""
     w = workload("b50kev_si_300k_reed")
     n = int(w["n_ions"])
     with R.Reed(w) as ctx:
-        ctx.run(n_ions=n, seed=0)
+        ctx.run(n_ions=n, seed=0, adaptive=True, n_initial=50, epoch_size=4096)
         st = ctx.stats()
         rec = ctx.records()
         bins, extra = ctx.profile()

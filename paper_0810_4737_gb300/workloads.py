@@ -15,7 +15,8 @@ The five workloads follow the synthetic cases of the REED-MD study:
     (1000 atoms, inner 27 cells integrated), rotation uniform in [0, 45) deg,
     100 depth bins of 1 nm (the throughput workload);
   * ``b50kev_si_300k_reed``  -- 65536 B ions, 50 keV, Si at 300 K, 12 cloning
-    depths with weights 2^-k, 400 bins of 2 nm;
+    depths with weights 2^-k (geometric 20-600 nm as the initial guess of an
+    adaptive run), 400 bins of 2 nm;
   * ``ar30kev_ceo2_300k_buck`` -- 16384 Ar ions, 30 keV, fluorite CeO2,
     4x4x4-cell window (768 atoms), Buckingham pairs with ZBL below 1 A,
     directions within 10 deg of [001], 64^3 damage voxels;

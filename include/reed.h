@@ -49,8 +49,9 @@ extern "C" {
 #define REED_E_STATE -8      /* call made in the wrong state (e.g. no run yet) */
 #define REED_E_NEIGHBOR -9   /* (reserved) */
 /* Positive codes: the run completed, with a counted anomaly (see reed_stats). */
-#define REED_W_NEIGHBOR 1    /* some atom had more target neighbours than a list holds: the
-                                surplus bonds were left out of its forces (nb_overflow) */
+#define REED_W_NEIGHBOR 1    /* some atom had more target neighbours than a list holds, or
+                                found no list slot: the surplus bonds were left out of its
+                                forces (nb_overflow, bond_cap_overflow) */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define REED_LATTICE_DIAMOND 0   /* 8-atom cubic cell, one species (Si) */

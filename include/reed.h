@@ -216,6 +216,8 @@ typedef struct {
     int32_t threads_per_track, ctas_per_sm, grid, smem_bytes;  /* last launch */
     int64_t splits[16];      /* clones made on first passing cloning depth k+1 (the
                                 paper's per-depth split statistics, Sec. 3) */
+    int64_t pooled;          /* clones run by another CTA than the one that made them
+                                (taken from the shared clone pool) */
 } reed_stats_t;
 
 typedef struct reed_ctx reed_ctx;

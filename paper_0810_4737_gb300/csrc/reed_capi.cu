@@ -72,6 +72,11 @@ struct reed_ctx {
     // clone stacks
     unsigned char* d_stacks = nullptr;
     size_t stacks_bytes = 0;
+    // shared clone pool: records, slot states and its two counters
+    unsigned char* d_pool = nullptr;
+    size_t pool_bytes = 0;
+    unsigned* d_pool_state = nullptr;   // pool slots + 3 control words
+    int pool_state_cap = 0;
     // scratch for diagnostics
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -545,7 +550,7 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     ctx->smem_optin = (size_t)optin;
     if (cudaMalloc((void**)&ctx->d_counters, sizeof(unsigned long long) * REED_NCOUNT) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->d_splits, sizeof(unsigned long long) * REED_MAX_THR) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_splits, sizeof(unsigned long long) * (REED_MAX_THR + 1)) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_wsum, sizeof(double) * 4) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_next, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void**)&ctx->d_status, sizeof(int)) != cudaSuccess ||
@@ -558,7 +563,7 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
         return fail(nullptr, REED_E_NOMEM, "device allocation failed");
     }
     cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT);
-    cudaMemset(ctx->d_splits, 0, sizeof(unsigned long long) * REED_MAX_THR);
+    cudaMemset(ctx->d_splits, 0, sizeof(unsigned long long) * (REED_MAX_THR + 1));
     cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4);
     cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long));
     {   // no cloning depth until one is set
@@ -686,6 +691,20 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
             ctx->stacks_bytes = need;
         }
         B.stacks = ctx->d_stacks;
+        // the shared pool: one record per CTA, taken by CTAs that run out of work
+        const size_t pool_need = B.entry_bytes * (size_t)L.grid;
+        if (pool_need > ctx->pool_bytes) {
+            if ((rc = dev_alloc(ctx, &ctx->d_pool, pool_need))) return rc;
+            ctx->pool_bytes = pool_need;
+        }
+        if (L.grid + 3 > ctx->pool_state_cap) {
+            if ((rc = dev_alloc(ctx, &ctx->d_pool_state, sizeof(unsigned) * (size_t)(L.grid + 3)))) return rc;
+            ctx->pool_state_cap = L.grid + 3;
+        }
+        B.pool = ctx->d_pool;
+        B.pool_state = ctx->d_pool_state;
+        B.pool_ctl = ctx->d_pool_state + L.grid;
+        B.pool_slots = L.grid;
     }
     B.hist = ctx->d_hist;
     B.counters = ctx->d_counters;
@@ -769,6 +788,9 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
             Pe.nthr = x.nthr;
             Pe.thr_from_device = ((o.adaptive || o.device_thresholds) && x.nthr > 0) ? 1 : 0;
             if ((e = cudaMemsetAsync(ctx->d_next, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+            if (B.pool &&
+                (e = cudaMemsetAsync(B.pool_state, 0, sizeof(unsigned) * (size_t)(B.pool_slots + 3), s)) != cudaSuccess)
+                return e;
             if (o.adaptive && x.nthr > 0) {
                 double* hrow = ctx->d_thr_hist + (size_t)REED_MAX_THR * row++;
                 if (x.update) {
@@ -817,6 +839,8 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     ctx->last_cfg = L;
     int status = 0;
     CK(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status & ERR_TIMEOUT)
+        return fail(ctx, REED_E_TIMEOUT, "an idle CTA stopped waiting for the shared clone pool: tracks may be missing");
     if (status & ERR_NONFINITE) return fail(ctx, REED_E_NONFINITE, "a track became non-finite (see reed_stats)");
     if (status & ERR_QUEUE) return fail(ctx, REED_E_QUEUE_FULL, "clone stack overflow: clones dropped");
     if (status & ERR_NEIGHBOR) {
@@ -839,7 +863,7 @@ int reed_range_profile(reed_ctx* ctx, double* bins_out, int n_bins, double* extr
 int reed_stats(reed_ctx* ctx, reed_stats_t* out)
 {
     if (!ctx || !out) return REED_E_ARG;
-    unsigned long long c[REED_NCOUNT], sp[REED_MAX_THR];
+    unsigned long long c[REED_NCOUNT], sp[REED_MAX_THR + 1];
     double w[4];
     CK(cudaMemcpy(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(sp, ctx->d_splits, sizeof(sp), cudaMemcpyDeviceToHost));
@@ -860,6 +884,7 @@ int reed_stats(reed_ctx* ctx, reed_stats_t* out)
     out->atom_updates = (int64_t)c[C_MOVED];
     for (int k = 0; k < REED_NPHASE; ++k) out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
     for (int k = 0; k < REED_MAX_THR; ++k) out->splits[k] = (int64_t)sp[k];
+    out->pooled = (int64_t)sp[REED_MAX_THR];
     out->failed = (int64_t)c[C_FAILED];
     out->stopped = (int64_t)c[C_STOP];
     out->backscattered = (int64_t)c[C_BACK];
@@ -1046,7 +1071,7 @@ int reed_reset(reed_ctx* ctx)
     ctx->d_grads = nullptr;
     ctx->grads_cap = 0;
     CK(cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * REED_NCOUNT));
-    CK(cudaMemset(ctx->d_splits, 0, sizeof(unsigned long long) * REED_MAX_THR));
+    CK(cudaMemset(ctx->d_splits, 0, sizeof(unsigned long long) * (REED_MAX_THR + 1)));
     CK(cudaMemset(ctx->d_wsum, 0, sizeof(double) * 4));
     CK(cudaMemset(ctx->d_rec_count, 0, sizeof(unsigned long long)));
     return REED_OK;
@@ -1057,7 +1082,7 @@ const char* reed_last_error(reed_ctx* ctx) { return ctx ? ctx->err.c_str() : g_i
 void reed_destroy(reed_ctx* ctx)
 {
     if (!ctx) return;
-    void* ptrs[] = {ctx->d_hist, ctx->d_counters, ctx->d_splits, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
+    void* ptrs[] = {ctx->d_pool, ctx->d_pool_state, ctx->d_hist, ctx->d_counters, ctx->d_splits, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
                     ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch,
                     ctx->d_thr, ctx->d_thr_hist, ctx->d_finished, ctx->d_damage, ctx->d_grads,
                     ctx->d_adj, ctx->d_kde};
@@ -1486,9 +1511,10 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
         stats_out->triplets = (int64_t)c[C_TRIPLETS];
         stats_out->atom_updates = (int64_t)c[C_MOVED];
         for (int k = 0; k < REED_NPHASE; ++k) stats_out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
-        unsigned long long sp[REED_MAX_THR];
+        unsigned long long sp[REED_MAX_THR + 1];
         CK(cudaMemcpy(sp, B.splits, sizeof(sp), cudaMemcpyDeviceToHost));
         for (int k = 0; k < REED_MAX_THR; ++k) stats_out->splits[k] = (int64_t)sp[k];
+        stats_out->pooled = (int64_t)sp[REED_MAX_THR];
         stats_out->w_stopped = w[W_STOPPED];
         stats_out->w_back = w[W_BACK];
         stats_out->w_trunc = w[W_TRUNC];

@@ -119,7 +119,14 @@ struct DevParams {
 struct DevBuf {
     double* hist;                   // nbins + 3 (under, over, back)
     unsigned long long* counters;   // REED_NCOUNT
-    unsigned long long* splits;     // clones made at each cloning level (REED_MAX_THR), may be null
+    unsigned long long* splits;     // clones made at each cloning level (REED_MAX_THR), then clones
+                                    // taken from the pool; may be null
+    // shared clone pool (may be null): CTAs that run out of work take clones
+    // that busy CTAs donate while some CTA is idle
+    unsigned char* pool;            // pool_slots x entry_bytes
+    unsigned* pool_state;           // per slot: POOL_EMPTY / WRITING / FULL / READING
+    unsigned* pool_ctl;             // [0] idle CTAs, [1] records reserved or held, [2] records published
+    int pool_slots;
     double* wsum;                   // W_*
     unsigned long long* next;       // primary queue head
     reed_track_record* records;
@@ -138,7 +145,7 @@ struct DevBuf {
     unsigned long long* finished;   // tracks finished in this run (stop rule)
 };
 
-enum { ERR_QUEUE = 1, ERR_NONFINITE = 2, ERR_NEIGHBOR = 4 };
+enum { ERR_QUEUE = 1, ERR_NONFINITE = 2, ERR_NEIGHBOR = 4, ERR_TIMEOUT = 8 };
 
 // ---------------------------------------------------------------------------
 // Precision-generic vector and math helpers.  The FP32 forms use the SFU

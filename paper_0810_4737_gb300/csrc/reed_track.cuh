@@ -30,7 +30,11 @@
 
 #include "reed_physics.cuh"
 
-enum { SRC_NONE = 0, SRC_PRIMARY = 1, SRC_CLONE = 2 };
+enum { SRC_NONE = 0, SRC_PRIMARY = 1, SRC_CLONE = 2, SRC_STOLEN = 3 };
+enum { POOL_EMPTY = 0, POOL_WRITING = 1, POOL_FULL = 2, POOL_READING = 3 };
+// polls of the clone pool by an idle CTA before it gives up (each sleeps up
+// to 4 us: about five minutes in all)
+#define REED_POOL_POLLS (1ll << 26)
 enum { EV_NONE = 0, EV_END = 1, EV_CLONE = 2, EV_CKPT = 3 };
 
 // Ion state as stored in shared memory and in clone records.  Position,
@@ -63,7 +67,7 @@ template <typename R> struct TrackShared {
     double gth[8];
     R adj_red[REED_MAX_WARPS][12];
     int Aold[3];
-    int shift, rebuild, event, status, src, top, nclone;
+    int shift, rebuild, event, status, src, top, nclone, slot;
     int need_count, active_count;
     int scan[2][REED_MAX_WARPS];
     long long pidx;
@@ -999,6 +1003,42 @@ __device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShar
 }
 
 // Copy the window (pos, vel, frc) between shared memory and a clone record.
+// ---------------------------------------------------------------------------
+// Shared clone pool (the paper's host handing returned clones to whichever
+// client is free, Sec. 3).  Lock-free: a slot is claimed with one CAS and no
+// CTA ever waits for a particular other CTA; an idle CTA polls the pool with a
+// bounded number of sleeps.  Records pass through L2 only (they are written
+// and read by different SMs).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pool_claim(const DevBuf& B, unsigned from, unsigned to)
+{
+    const int n = B.pool_slots;
+    const int start = (int)((blockIdx.x * 2654435761u) % (unsigned)n);
+    for (int j = 0; j < n; ++j) {
+        int s = start + j;
+        if (s >= n) s -= n;
+        if (*(volatile unsigned*)&B.pool_state[s] != from) continue;
+        if (atomicCAS(&B.pool_state[s], from, to) == from) return s;
+    }
+    return -1;
+}
+
+template <typename R, int TT>
+__device__ __forceinline__ void copy_window_cg(const DevParams& P, Win<R, TT>& W, const unsigned char* rec)
+{
+    using L = Layout<R, TT>;
+    const uint4* g = reinterpret_cast<const uint4*>(rec + L::align(sizeof(IonState<R>)));
+    const int na = P.na, w = (int)(sizeof(V4<R>) / sizeof(uint4));
+    uint4* pos = reinterpret_cast<uint4*>(W.pos);
+    uint4* vel = reinterpret_cast<uint4*>(W.vel);
+    uint4* frc = reinterpret_cast<uint4*>(W.frc);
+    for (int i = threadIdx.x; i < na * w; i += blockDim.x) {
+        pos[i] = __ldcg(g + i);
+        vel[i] = __ldcg(g + na * w + i);
+        frc[i] = __ldcg(g + 2 * na * w + i);
+    }
+}
+
 template <typename R, int TT>
 __device__ __forceinline__ void copy_window(const DevParams& P, Win<R, TT>& W, unsigned char* rec, bool to_rec)
 {
@@ -1113,6 +1153,33 @@ __global__ void __launch_bounds__(256, (track_min_ctas<R, TT, ADJ>())) reed_trac
                 S->pidx = (long long)k;
                 S->src = ((long long)k < P.n_primaries) ? SRC_PRIMARY : SRC_NONE;
             }
+            if (S->src == SRC_NONE && B.pool) {
+                // out of work: take a donated clone, or stop once every CTA is
+                // idle and no record is reserved or held
+                bool idle = false;
+                for (long long it = 0;; ++it) {
+                    // scan the slots only when some record is published
+                    const int sl = *(volatile unsigned*)&B.pool_ctl[2] > 0u ? pool_claim(B, POOL_FULL, POOL_READING) : -1;
+                    if (sl >= 0) {
+                        atomicSub(&B.pool_ctl[2], 1u);
+                        if (idle) atomicSub(&B.pool_ctl[0], 1u);
+                        S->slot = sl;
+                        S->src = SRC_STOLEN;
+                        break;
+                    }
+                    if (!idle) {
+                        atomicAdd(&B.pool_ctl[0], 1u);
+                        idle = true;
+                    }
+                    if (*(volatile unsigned*)&B.pool_ctl[0] >= gridDim.x && *(volatile unsigned*)&B.pool_ctl[1] == 0u)
+                        break;
+                    if (it >= REED_POOL_POLLS) {
+                        atomicOr(B.status, ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(it < 64 ? 500u : 4000u);
+                }
+            }
         }
         __syncthreads();
         const int src = S->src;
@@ -1142,6 +1209,28 @@ __global__ void __launch_bounds__(256, (track_min_ctas<R, TT, ADJ>())) reed_trac
                     __syncthreads();
                 }
             }
+        } else if (src == SRC_STOLEN) {
+            const unsigned char* rec = B.pool + (size_t)S->slot * B.entry_bytes;
+            if (tid == 0) {
+                __threadfence();
+                const uint4* h = reinterpret_cast<const uint4*>(rec);
+                uint4* d = reinterpret_cast<uint4*>(&S->ion);
+                for (int k = 0; k < (int)(sizeof(IonState<R>) / sizeof(uint4)); ++k) d[k] = __ldcg(h + k);
+                set_frame<R>(P, S);
+            }
+            copy_window_cg<R, TT>(P, W, rec);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(&B.pool_state[S->slot], (unsigned)POOL_EMPTY);
+                atomicSub(&B.pool_ctl[1], 1u);
+                if (B.splits) atomicAdd(&B.splits[REED_MAX_THR], 1ull);
+            }
+            if constexpr (TT != REED_TT_NONE) {
+                build_neighbours<R, TT>(P, H, W, nbovf, capovf);
+                if (tid == 0) ++c_rebuild;
+            }
+            __syncthreads();
         } else {
             unsigned char* rec = stack + (size_t)(S->top - 1) * B.entry_bytes;
             if (tid == 0) {
@@ -1298,6 +1387,38 @@ __global__ void __launch_bounds__(256, (track_min_ctas<R, TT, ADJ>())) reed_trac
             const int nc = S->nclone;
             __syncthreads();
             for (int c = 0; c < nc; ++c) {
+                // some CTA is idle: donate this clone to the pool instead
+                if (tid == 0) {
+                    S->slot = -1;
+                    if (B.pool && *(volatile unsigned*)&B.pool_ctl[0] > 0u) {
+                        atomicAdd(&B.pool_ctl[1], 1u);   // counted before the slot is visible
+                        S->slot = pool_claim(B, POOL_EMPTY, POOL_WRITING);
+                        if (S->slot < 0) atomicSub(&B.pool_ctl[1], 1u);
+                    }
+                }
+                __syncthreads();
+                if (S->slot >= 0) {
+                    unsigned char* rec = B.pool + (size_t)S->slot * B.entry_bytes;
+                    if (tid == 0) {
+                        IonState<R>& I = S->ion;
+                        I.level += 1;
+                        IonState<R> C = I;
+                        C.id = clone_id(I.id, I.level);
+                        C.key = track_key(P.seed, C.id);
+                        *reinterpret_cast<IonState<R>*>(rec) = C;
+                        ++c_clone;
+                        if (B.splits) atomicAdd(&B.splits[min(I.level, REED_MAX_THR) - 1], 1ull);
+                    }
+                    copy_window<R, TT>(P, W, rec, true);
+                    __threadfence();
+                    __syncthreads();
+                    if (tid == 0) {
+                        atomicExch(&B.pool_state[S->slot], (unsigned)POOL_FULL);
+                        atomicAdd(&B.pool_ctl[2], 1u);
+                    }
+                    __syncthreads();
+                    continue;
+                }
                 if (S->top >= B.stack_depth || stack == nullptr) {
                     if (tid == 0) {
                         c_drop += (unsigned long long)(nc - c);

@@ -82,7 +82,7 @@ class reed_stats_t(C.Structure):
         "triplets", "atom_updates")] + [("phase_cycles", C.c_int64 * 6)] + \
         [("w_stopped", C.c_double), ("w_back", C.c_double), ("w_trunc", C.c_double), ("kernel_ms", C.c_double),
          ("threads_per_track", C.c_int32), ("ctas_per_sm", C.c_int32), ("grid", C.c_int32),
-         ("smem_bytes", C.c_int32), ("splits", C.c_int64 * 16)]
+         ("smem_bytes", C.c_int32), ("splits", C.c_int64 * 16), ("pooled", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

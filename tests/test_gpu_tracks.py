@@ -141,6 +141,8 @@ def test_cloning_conserves_weight_and_statistics(R, O):
     assert st["dropped_clones"] == 0
     # per-depth split statistics: every clone counted once, at a used depth
     assert sum(st["splits"]) == st["clones"] and not any(st["splits"][6:])
+    # CTAs that ran out of primaries took clones from the shared pool
+    assert 0 < st["pooled"] <= st["clones"]
     assert len(np.unique(rec["id"])) == len(rec)
     # every lineage has exactly one primary record
     assert np.sum(rec["id"] == rec["primary"]) == n
@@ -235,6 +237,7 @@ def test_rare_event_workload_full_size(R):
         bins, extra = ctx.profile()
     assert st["primaries"] == n and st["dropped_clones"] == 0 and st["failed"] == 0
     assert st["tracks"] == n + st["clones"] == len(rec) and st["clones"] > n
+    assert st["pooled"] > 0
     wts = np.ldexp(1.0, -rec["level"].astype(int))
     assert np.sum(wts) == n
     assert bins.sum() + extra.sum() + st["w_trunc"] == n

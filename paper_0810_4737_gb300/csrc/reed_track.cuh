@@ -130,6 +130,10 @@ template <typename R, int TT> struct Win {
     V2<R>* bond;          // per slot and neighbour: {1/2 dV/db db/dzeta, dV/dr}
     V4<R>* xbar;          // adjoint of positions (adjoint runs)
     V4<R>* vbar;          // adjoint of velocities
+    // Neighbour q of list slot k is nbr[k * nb_slot + q * nb_q]: slot-major for
+    // Tersoff (a thread walks its own short list), neighbour-major for the
+    // 64-entry pair lists (consecutive slots, i.e. lanes, hit consecutive words).
+    int nb_slot, nb_q;
     // zero the bin counters (all threads; a barrier must follow)
     __device__ void clear_grid(const DevParams& P)
     {
@@ -137,6 +141,7 @@ template <typename R, int TT> struct Win {
             for (int b = threadIdx.x; b < P.g_nbins; b += blockDim.x) bin_count[b] = 0u;
     }
     __device__ Win(unsigned char* base, int na, int cap, int adj = 0, int nbins = 0)
+        : nb_slot(TT == REED_TT_BUCKINGHAM ? 1 : maxnb(TT)), nb_q(TT == REED_TT_BUCKINGHAM ? cap : 1)
     {
         using L = Layout<R, TT>;
         S = reinterpret_cast<TrackShared<R>*>(base);
@@ -333,7 +338,8 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
                                       int& overflow)
 {
     const V4<R> pi = W.pos[i];
-    uint16_t* out = W.nbr + (size_t)slot * maxnb(TT);
+    uint16_t* out = W.nbr + (size_t)slot * W.nb_slot;
+    const int oq = W.nb_q;
     int cnt = 0;
     const int nb = P.g_nb;
     const int bx = grid_axis<R>(P, H, pi.x), by = grid_axis<R>(P, H, pi.y), bz = grid_axis<R>(P, H, pi.z);
@@ -349,7 +355,7 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
                 const V4<R> pj = W.pos[j];
                 const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                 if (dx * dx + dy * dy + dz * dz < H.rlist2) {
-                    if (cnt < maxnb(TT)) out[cnt++] = (uint16_t)j;
+                    if (cnt < maxnb(TT)) out[(size_t)(cnt++) * oq] = (uint16_t)j;
                     else ++overflow;
                     if (TT == REED_TT_TERSOFF && !is_active(pj) && W.need_map[j] == REED_NO_SLOT)
                         W.need_map[j] = (uint16_t)REED_PENDING;
@@ -664,10 +670,11 @@ __device__ R pair_force(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& F
     const int m = W.nnb[k];
     const V4<R> pi = W.pos[i];
     const int si = species_of(pi);
-    const uint16_t* nb = W.nbr + (size_t)k * maxnb(TT);
+    const uint16_t* nb = W.nbr + (size_t)k * W.nb_slot;
+    const int oq = W.nb_q;
     R E = R(0);
     for (int q = 0; q < m; ++q) {
-        const V4<R> pj = W.pos[nb[q]];
+        const V4<R> pj = W.pos[nb[(size_t)q * oq]];
         R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
         R r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= H.b_rc2) continue;

@@ -126,7 +126,7 @@ typedef struct {
     double thresholds[16];   /* ascending cloning depths d_1..d_k, A */
     double bin_width;        /* A (fixed by the first run after init/reset) */
     int64_t first_id;        /* id of the first primary of this run (ids are the RNG streams) */
-    int32_t threads_per_track; /* 0 = autotune, else 32/64/128/256 */
+    int32_t threads_per_track; /* 0 = tuned or default, else 32/64/128/256 (512: pair-list model) */
     int32_t ctas_per_sm;       /* 0 = autotune / maximum occupancy */
     int32_t record_tracks;     /* 1: keep one reed_track_record per finished track */
     int32_t trace_tracks;      /* record the first trace_steps steps of primaries */
@@ -317,8 +317,9 @@ int reed_get_thresholds(reed_ctx* ctx, double* out16);
 /* Launch-configuration autotuner (the batching form's tuning): runs
  * n_trial primaries of the given beam (ids from 2^40 up, so no primary of a
  * real run is repeated) once per candidate -- threads_per_track in {32, 64,
- * 128, 256} and, for each, CTAs per SM at the occupancy maximum, three
- * quarters and half of it -- and keeps the fastest (ion-steps per second of
+ * 128, 256, and 512 where the model allows it} and, for each, CTAs per SM
+ * at the occupancy maximum, three quarters and half of it -- and keeps the
+ * fastest (ion-steps per second of
  * kernel time) for later runs of this context whose opt->threads_per_track
  * and opt->ctas_per_sm are 0 and whose precision and adjoint flag match opt.
  * The trials run in a private context, so this context's tallies are not

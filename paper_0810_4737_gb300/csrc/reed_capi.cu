@@ -395,7 +395,7 @@ int ensure_tallies(reed_ctx* ctx, int nbins, double bin_w)
     return REED_OK;
 }
 
-bool valid_threads(int t) { return t == 32 || t == 64 || t == 128 || t == 256; }
+bool valid_threads(int t) { return t == 32 || t == 64 || t == 128 || t == 256 || t == 512; }
 
 }  // namespace
 
@@ -1117,8 +1117,8 @@ int reed_autotune(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, d
     if (ai) o.record_tracks = 1;
     int best_t = 0, best_c = 0, n = 0;
     double best = -1.0;
-    static const int kThreads[4] = {32, 64, 128, 256};
-    for (int ti = 0; ti < 4; ++ti) {
+    static const int kThreads[5] = {32, 64, 128, 256, 512};
+    for (int ti = 0; ti < 5; ++ti) {
         // the occupancy maximum for this thread count: a run with ctas_per_sm
         // far above it is clamped to it
         reed_run_opts probe = o;

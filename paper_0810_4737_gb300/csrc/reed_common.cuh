@@ -17,7 +17,7 @@
 
 #define REED_MAX_BASIS 12
 #define REED_MAX_THR 16
-#define REED_MAX_WARPS 8
+#define REED_MAX_WARPS 16
 #define REED_MAXNB 12           // Tersoff neighbours kept per atom
 #define REED_MAXNB_PAIR 64      // pair-potential neighbours kept per atom
 

@@ -1113,8 +1113,12 @@ constexpr int track_min_ctas()
     return TT == REED_TT_TERSOFF && sizeof(R) == 4 ? 2 : 1;
 }
 
+// Threads per track at most: 512 for the pair-list model (one track fills an
+// SM's shared memory, so its warps are all the SM gets), else 256.
+template <int TT> constexpr int track_max_threads() { return TT == REED_TT_BUCKINGHAM ? 512 : 256; }
+
 template <typename R, int TT, bool ADJ>
-__global__ void __launch_bounds__(256, (track_min_ctas<R, TT, ADJ>())) reed_track_kernel(
+__global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, TT, ADJ>())) reed_track_kernel(
     const __grid_constant__ DevParams P, const __grid_constant__ DevBuf B)
 {
     static_assert(!ADJ || TT == REED_TT_NONE, "the adjoint runs without target-target forces");

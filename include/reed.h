@@ -256,22 +256,34 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
  * REED_E_ARG. */
 int reed_range_profile(reed_ctx* ctx, double* bins_out, int n_bins, double* extra3);
 
-/* Per-track sensitivities dz/dtheta (8 doubles per record, in record order;
- * zero for tracks that did not stop) of adjoint runs: out (host or device)
- * receives up to cap rows; *n_out (host) the number of rows kept. */
+/* Truncated-segment sensitivities (the differentiable range profile; the
+ * paper has no counterpart -- its profiles feed a fit of stopping models,
+ * Sec. 4).  theta = (s_e, s_loc, spline_c[0..5]) as in reed_potentials.
+ *
+ * Per-track dz_T/dtheta (8 doubles per record, in record order; zero for
+ * tracks that did not stop) of adjoint runs (opt->adjoint): out (host or
+ * device, may be NULL to query the count) receives up to cap rows; *n_out
+ * (host) the number of rows kept.  REED_E_STATE if no adjoint run since
+ * init/reset, REED_E_ARG on a null n_out or a negative cap. */
 int reed_track_grads(reed_ctx* ctx, double* out, int64_t cap, int64_t* n_out);
 
 /* Kernel-density range profile of the stopped tracks recorded since
  * init/reset: p[b] = sum_i w_i N(z_b; z_i, sigma) / sum_i w_i at bin centres
- * z_b = (b + 1/2) bin_width (A^-1); p_out host or device, n_bins doubles. */
+ * z_b = (b + 1/2) bin_width (A^-1, w_i = 2^-level); p_out host or device,
+ * n_bins doubles.  Needs records (opt->record_tracks): REED_E_STATE without,
+ * REED_E_ARG for sigma or bin_width <= 0 or n_bins < 1.  Sums in record
+ * order, so two runs agree to rounding, not bit for bit. */
 int reed_kde_profile(reed_ctx* ctx, double sigma, int n_bins, double bin_width, double* p_out);
 
-/* Gradient of a loss of that profile: dL_dtheta[8] (host) =
+/* Gradient of a loss of that profile: dL_dtheta[8] (host or device) =
  * sum_i (sum_b dL_dp[b] dp_b/dz_i) dz_i/dtheta, from the per-track
- * sensitivities of an adjoint run; dL_dp host or device, n_bins doubles. */
+ * sensitivities of an adjoint run (the weights and sum_i w_i do not depend
+ * on theta); dL_dp host or device, n_bins doubles.  REED_E_STATE if no
+ * adjoint run since init/reset, REED_E_ARG as for reed_kde_profile. */
 int reed_grad(reed_ctx* ctx, double sigma, int n_bins, double bin_width, const double* dL_dp, double* dL_dtheta);
 
-/* Set theta = (s_e, s_loc, spline_c[0..5]) of the context's potentials. */
+/* Set theta = (s_e, s_loc, spline_c[0..5]) of the context's potentials for
+ * later runs (host, 8 doubles).  REED_E_ARG on a null pointer. */
 int reed_set_theta(reed_ctx* ctx, const double* theta8);
 
 /* Cumulative damage map of all runs since init/reset: out (host or device)

@@ -256,9 +256,11 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
  * REED_E_ARG. */
 int reed_range_profile(reed_ctx* ctx, double* bins_out, int n_bins, double* extra3);
 
-/* Truncated-segment sensitivities (the differentiable range profile; the
- * paper has no counterpart -- its profiles feed a fit of stopping models,
- * Sec. 4).  theta = (s_e, s_loc, spline_c[0..5]) as in reed_potentials.
+/* Truncated-segment sensitivities of the range profile for fitting model
+ * parameters to measured profiles (the paper notes REED-MD profiles match
+ * measurements with minimal empirical fitting of model parameters, Sec. 1;
+ * it computes no sensitivities itself).  theta = (s_e, s_loc,
+ * spline_c[0..5]) as in reed_potentials.
  *
  * Per-track dz_T/dtheta (8 doubles per record, in record order; zero for
  * tracks that did not stop) of adjoint runs (opt->adjoint): out (host or

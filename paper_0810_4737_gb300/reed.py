@@ -423,7 +423,7 @@ class Reed:
     def run(self, n_ions=None, seed=None, precision=PREC_MIXED, tolerate=(), **kw):
         """Run primaries; anomaly codes listed in `tolerate` (e.g. E_NEIGHBOR)
         are returned instead of raised (the run is complete, see stats())."""
-        w = self.w
+        w = dict(self.w, step_cap=kw.pop("step_cap", self.w["step_cap"]))
         o = run_opts(w, precision=precision, **kw)
         ion = w["ion"]
         rc = lib().reed_run(self.ctx, ion["Z"], ion["M"], w["energy"], w["tilt"], w["rot"][0], w["rot"][1],

@@ -253,3 +253,35 @@ def test_rare_event_workload_full_size(R):
     tot = bins.sum()
     assert bins[bins > 0].min() / tot < 1e-7 < 1.0 / n
     assert np.count_nonzero(bins) > np.count_nonzero(pbins)
+
+
+def test_limits_and_errors(R):
+    """The largest windows run or are refused cleanly; calls in the wrong
+    state and bad arguments return their codes and leave the context usable."""
+    # the largest window (6^3 cells) with ion-target forces only
+    w6 = workload("b1kev_si_0k_zbl", n=6, sigma=0.076, rot=(0.0, 45.0))
+    with R.Reed(w6) as ctx:
+        ctx.run(n_ions=64, seed=1)
+        st = ctx.stats()
+        assert st["tracks"] == 64 and st["failed"] == 0
+    # a 6^3-cell Tersoff window (1728 atoms) needs more shared memory than a
+    # CTA can have, in either form: refused up front
+    wt = workload("as10kev_si_300k_tersoff", n=6)
+    with R.Reed(wt) as ctx:
+        for prec in (0, 1):
+            with pytest.raises(R.ReedError) as e:
+                ctx.run(n_ions=1, precision=prec)
+            assert e.value.code == R.E_SMEM
+    w = workload("b1kev_si_0k_zbl")
+    with R.Reed(w) as ctx:
+        with pytest.raises(R.ReedError) as e:
+            ctx.profile()                           # no run yet
+        assert e.value.code == R.E_STATE
+        with pytest.raises(R.ReedError) as e:
+            ctx.run(n_ions=4, adjoint=True, record=False)   # sensitivities need records
+        assert e.value.code == R.E_ARG
+        with pytest.raises(R.ReedError) as e:
+            ctx.run(n_ions=4, adjoint=True, adj_segment=250, adj_every=20)   # not a multiple
+        assert e.value.code == R.E_ARG
+        ctx.run(n_ions=4, seed=1)                   # still usable
+        assert ctx.stats()["tracks"] == 4

@@ -60,6 +60,8 @@ class Params(C.Structure):
         ("nbins", C.c_int), ("bin_w", C.c_double),
         ("dn", C.c_int), ("dvox", C.c_double), ("dmin", C.c_double),
         ("de_max", C.c_double),
+        ("dose_scale", C.c_double), ("fb_ec", C.c_double), ("sigma_am", C.c_double),
+        ("fb_map", C.c_void_p),
     ]
 
 
@@ -189,6 +191,20 @@ def params(w: dict, screening: int = 1) -> Params:
     p.nbins, p.bin_w = int(w["n_bins"]), float(w["bin_w"])
     p.dn, p.dvox, p.dmin = int(w.get("damage_n", 0)), float(w.get("damage_voxel", 10.0)), float(w.get("damage_min", 0.1))
     p.de_max = float(w.get("de_max", 0.0))
+    p.dose_scale = float(w.get("dose_scale", 0.0))
+    p.fb_ec = float(w.get("e_crit", 0.0))
+    p.sigma_am = float(w.get("sigma_amorphous", 0.0))
+    p.fb_map = None
+    return p
+
+
+def set_feedback_map(p: Params, damage_map):
+    """Damage map (dn^3 voxels + overflow, FP64) read by cell creation when
+    damage feedback is on; the array is kept alive on the Params object."""
+    a = np.ascontiguousarray(damage_map, dtype=np.float64).ravel()
+    assert a.size == p.dn ** 3 + 1
+    p._fb_keep = a
+    p.fb_map = a.ctypes.data
     return p
 
 
@@ -272,7 +288,7 @@ def launch_state(p: Params, seed: int, track_id: int):
 
 
 def run(p: Params, n_ions: int, seed: int, first_id: int = 0, threads: int | None = None,
-        records: bool = True):
+        records: bool = True, damage_init=None):
     """Run primaries [first_id, first_id+n_ions); returns a dict with the
     histogram (nbins + under/over/back), counters and per-track records."""
     nb = p.nbins + 3
@@ -284,6 +300,8 @@ def run(p: Params, n_ions: int, seed: int, first_id: int = 0, threads: int | Non
     ptr = C.c_void_p()
     nrec = C.c_int64(0)
     dmg = np.zeros(p.dn ** 3 + 1) if p.dn > 0 else None
+    if dmg is not None and damage_init is not None:
+        dmg[:] = np.asarray(damage_init, dtype=np.float64).ravel()   # cumulative map before this run
     lib().o_run_damage(C.byref(p), n_ions, first_id, seed, threads, _dp(hist),
                        cnt.ctypes.data_as(C.POINTER(C.c_int64)), _dp(wt),
                        C.byref(ptr) if records else None, C.byref(nrec), _dp(dmg) if dmg is not None else None)

@@ -98,6 +98,11 @@ typedef struct {
     double dvox, dmin;
     /* energy term of the adaptive step (eV per step; 0 = off) */
     double de_max;
+    /* damage feedback (reading, see o_cell_atoms): on when fb_ec > 0 and
+     * fb_map is set; fb_map holds the dn^3 (+ overflow) map as it stood when
+     * the run started */
+    double dose_scale, fb_ec, sigma_am;
+    const double* fb_map;
 } o_params;
 
 typedef struct {
@@ -153,6 +158,7 @@ uint64_t o_child_id(uint64_t parent, int level)
 
 #define O_TAG_CELL 1u
 #define O_TAG_LAUNCH 2u
+#define O_TAG_DAMAGE 3u
 
 static void o_draw(uint64_t key, int32_t ix, int32_t iy, int32_t iz, uint32_t word, uint32_t out[4])
 {
@@ -190,6 +196,33 @@ int o_basis_count(int lattice) { return lattice == 1 ? 12 : (lattice == 0 ? 8 : 
 
 static int o_basis_species(int lattice, int b) { return (lattice == 1 && b >= 4) ? 1 : 0; }
 
+/* reading (damage feedback; the paper feeds cumulative damage back to the
+ * tracks, Sec. 1 and 3, without giving the mechanism): a cell created where
+ * the cumulative damage map holds D (eV) in the voxel of the cell's centre
+ * is amorphous with probability 1 - exp(-e / fb_ec), e = dose_scale * D / N
+ * the energy deposited per target atom (N = atoms of the perfect lattice in
+ * one voxel); an amorphous cell's atoms are displaced by sigma_am instead of
+ * sigma.  The decision uses its own Philox block (tag 3) of the cell. */
+static double o_cell_sigma(const o_params* P, uint64_t key, int32_t ix, int32_t iy, int32_t iz)
+{
+    if (!(P->fb_ec > 0.0) || !P->fb_map || P->dn <= 0) return P->sigma;
+    double half = 0.5 * P->dn * P->dvox;
+    int v[3];
+    double c[3] = {(ix + 0.5) * P->a + half, (iy + 0.5) * P->a + half, (iz + 0.5) * P->a};
+    for (int d = 0; d < 3; ++d) {
+        v[d] = (int)floor(c[d] / P->dvox);
+        if (v[d] < 0 || v[d] >= P->dn) return P->sigma;
+    }
+    double D = P->fb_map[((size_t)v[0] * P->dn + v[1]) * P->dn + v[2]];
+    double cells_per_voxel = pow(P->dvox / P->a, 3.0);
+    double N = o_basis_count(P->lattice) * cells_per_voxel;
+    double e = P->dose_scale * D / N;
+    double pam = 1.0 - exp(-e / P->fb_ec);
+    uint32_t w[4];
+    o_draw(key, ix, iy, iz, O_TAG_DAMAGE, w);
+    return o_unit(w[0]) < pam ? P->sigma_am : P->sigma;
+}
+
 /* Atoms of absolute cell (ix,iy,iz), absolute coordinates.  Cells with
  * iz < 0 lie above the surface and are empty (target occupies z >= 0).
  * Returns the number of atoms written. */
@@ -199,16 +232,17 @@ int o_cell_atoms(const o_params* P, uint64_t key, int32_t ix, int32_t iy, int32_
     if (iz < 0) return 0;
     int nb = o_basis_count(P->lattice);
     const double(*B)[3] = P->lattice == 1 ? O_FLUORITE : O_DIAMOND;
+    double sig = o_cell_sigma(P, key, ix, iy, iz);
     for (int b = 0; b < nb; ++b) {
         double g[3] = {0.0, 0.0, 0.0};
-        if (P->sigma > 0.0) {
+        if (sig > 0.0) {
             uint32_t w[4];
             o_draw(key, ix, iy, iz, ((uint32_t)b << 4) | O_TAG_CELL, w);
             o_gauss3(w, g);
         }
-        xyz[3 * b + 0] = (ix + B[b][0]) * P->a + P->sigma * g[0];
-        xyz[3 * b + 1] = (iy + B[b][1]) * P->a + P->sigma * g[1];
-        xyz[3 * b + 2] = (iz + B[b][2]) * P->a + P->sigma * g[2];
+        xyz[3 * b + 0] = (ix + B[b][0]) * P->a + sig * g[0];
+        xyz[3 * b + 1] = (iy + B[b][1]) * P->a + sig * g[1];
+        xyz[3 * b + 2] = (iz + B[b][2]) * P->a + sig * g[2];
         sp[b] = o_basis_species(P->lattice, b);
     }
     return nb;
@@ -981,6 +1015,15 @@ int o_run_damage(const o_params* P, int64_t n_ions, int64_t first_id, uint64_t s
     o_consts_init(P, &K);
     int nb = P->nbins + 3;
     size_t nd = (damage && P->dn > 0) ? (size_t)P->dn * P->dn * P->dn + 1 : 0;
+    /* damage feedback reads the map as it stood when the run started */
+    o_params PF = *P;
+    double* snap = NULL;
+    if (nd && P->fb_ec > 0.0) {
+        snap = (double*)malloc(nd * sizeof(double));
+        memcpy(snap, damage, nd * sizeof(double));
+        PF.fb_map = snap;
+    }
+    P = &PF;
     o_recbuf* bufs = recs_out ? (o_recbuf*)calloc((size_t)n_ions, sizeof(o_recbuf)) : NULL;
     int nt = nthreads > 0 ? nthreads : 1;
     double* hs = (double*)calloc((size_t)nt * nb, sizeof(double));
@@ -1029,6 +1072,7 @@ int o_run_damage(const o_params* P, int64_t n_ions, int64_t first_id, uint64_t s
     free(cs);
     free(ws);
     free(ds);
+    free(snap);
     return 0;
 }
 

@@ -349,6 +349,27 @@ int reed_autotune(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, d
                   double rot_deg_hi, int64_t n_trial, uint64_t seed, const reed_run_opts* opt, reed_tune_entry* table,
                   int cap, int* n_out);
 
+/* Damage feedback (a reading of the paper's cumulative damage information
+ * fed back to the tracks, Sec. 1 and 3; the mechanism is not given there):
+ * while e_crit > 0 and the context holds a damage map, a newly created cell
+ * is amorphous with probability 1 - exp(-e / e_crit), where e = dose_scale *
+ * D / N is the energy deposited per target atom in the map voxel D that
+ * holds the cell's centre (N = lattice atoms per voxel, dose_scale = physical
+ * ions each simulated primary stands for); an amorphous cell's atoms get
+ * Gaussian offsets of sigma_amorphous (A) instead of the lattice's sigma.
+ * The decision uses its own Philox block of the cell (tag 3).  Each launch
+ * reads the map as it stood when the launch started (epochs of an adaptive
+ * run see the damage of the epochs before them), so results do not depend on
+ * timing.  e_crit = 0 turns it off.  REED_E_ARG on negative values. */
+int reed_set_damage_feedback(reed_ctx* ctx, double dose_scale, double e_crit, double sigma_amorphous);
+
+/* Replace the context's cumulative damage map: map (host or device) holds
+ * n^3 voxels of voxel A ([ix][iy][iz], x and y centred on the entry cell, z
+ * from the surface) and the overflow, as reed_damage_map returns it, e.g. the
+ * sum of several processes' maps.  Later runs must use the same n and voxel.
+ * REED_E_ARG for n outside 1..512 or voxel <= 0. */
+int reed_set_damage_map(reed_ctx* ctx, const double* map, int n, double voxel);
+
 /* Measured throughput of the units that bound the track stepper, on the
  * current device (microbenchmarks of independent instruction streams, a few
  * tenths of a second in all): FP32 and FP64 FMA, the SFU's ex2 and rsqrt,

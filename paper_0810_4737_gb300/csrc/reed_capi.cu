@@ -97,6 +97,10 @@ struct reed_ctx {
     int thr_hist_cap = 0, thr_epochs = 0;
     unsigned long long* d_finished = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    // damage feedback settings (e_crit <= 0: off) and the per-launch snapshot
+    double fb_dose = 0.0, fb_ec = 0.0, fb_sam = 0.0;
+    double* d_dsnap = nullptr;
+    size_t dsnap_bytes = 0;
     // autotuned launch configuration per [precision][adjoint] (0 = none)
     int tuned_threads[2][2] = {{0, 0}, {0, 0}};
     int tuned_ctas[2][2] = {{0, 0}, {0, 0}};
@@ -356,6 +360,22 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     fill_hot<double>(P.hd, P, ctx, skin);
     P.bond_cap = bond_capacity(P, skin);
     return REED_OK;
+}
+
+// Damage feedback fields of the parameters: on when the context has
+// settings and a map; map = the cumulative map the created cells read.
+void set_feedback(const reed_ctx* ctx, DevParams& P, const double* map)
+{
+    P.fb_map = nullptr;
+    if (!(ctx->fb_ec > 0.0) || !ctx->d_damage || !map) return;
+    P.fb_map = map;
+    P.fb_n = ctx->dn;
+    P.fb_vox = ctx->dvox;
+    P.fb_half = 0.5 * ctx->dn * ctx->dvox;
+    P.fb_dose = ctx->fb_dose;
+    P.fb_atoms = basis_count(ctx->lat.kind) * std::pow(ctx->dvox / ctx->lat.a, 3.0);
+    P.fb_ec = ctx->fb_ec;
+    P.sigma_am = ctx->fb_sam;
 }
 
 reed_run_opts default_opts()
@@ -775,6 +795,17 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     }
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
     CK(cudaMemsetAsync(ctx->d_finished, 0, sizeof(unsigned long long), st));
+    // damage feedback: every launch reads a snapshot of the cumulative map
+    // taken as it starts, so a launch's tracks do not depend on timing
+    size_t snap_bytes = 0;
+    if (ctx->fb_ec > 0.0 && ctx->d_damage) {
+        snap_bytes = sizeof(double) * ((size_t)ctx->dn * ctx->dn * ctx->dn + 1);
+        if (snap_bytes > ctx->dsnap_bytes) {
+            if ((rc = dev_alloc(ctx, &ctx->d_dsnap, snap_bytes))) return rc;
+            ctx->dsnap_bytes = snap_bytes;
+        }
+        set_feedback(ctx, P, ctx->d_dsnap);
+    }
 
     // the device work of the run, on stream s
     auto enqueue = [&](cudaStream_t s) -> cudaError_t {
@@ -788,6 +819,10 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
             Pe.nthr = x.nthr;
             Pe.thr_from_device = ((o.adaptive || o.device_thresholds) && x.nthr > 0) ? 1 : 0;
             if ((e = cudaMemsetAsync(ctx->d_next, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+            if (snap_bytes &&
+                (e = cudaMemcpyAsync(ctx->d_dsnap, ctx->d_damage, snap_bytes, cudaMemcpyDeviceToDevice, s)) !=
+                    cudaSuccess)
+                return e;
             if (B.pool &&
                 (e = cudaMemsetAsync(B.pool_state, 0, sizeof(unsigned) * (size_t)(B.pool_slots + 3), s)) != cudaSuccess)
                 return e;
@@ -1024,6 +1059,29 @@ int reed_thresholds(reed_ctx* ctx, double* history, int max_epochs, int* n_epoch
     return REED_OK;
 }
 
+int reed_set_damage_feedback(reed_ctx* ctx, double dose_scale, double e_crit, double sigma_amorphous)
+{
+    if (!ctx || !(dose_scale >= 0.0) || !(e_crit >= 0.0) || !(sigma_amorphous >= 0.0)) return REED_E_ARG;
+    ctx->fb_dose = dose_scale;
+    ctx->fb_ec = e_crit;
+    ctx->fb_sam = sigma_amorphous;
+    return REED_OK;
+}
+
+int reed_set_damage_map(reed_ctx* ctx, const double* map, int n, double voxel)
+{
+    if (!ctx || !map || n < 1 || n > 512 || !(voxel > 0.0)) return REED_E_ARG;
+    const size_t nd = (size_t)n * n * n + 1;
+    int rc;
+    if (!ctx->d_damage || ctx->dn != n) {
+        if ((rc = dev_alloc(ctx, &ctx->d_damage, sizeof(double) * nd))) return rc;
+    }
+    ctx->dn = n;
+    ctx->dvox = voxel;
+    CK(cudaMemcpy(ctx->d_damage, map, sizeof(double) * nd, cudaMemcpyDefault));
+    return REED_OK;
+}
+
 int reed_update_thresholds(reed_ctx* ctx, const double* hist, int n_bins, double bin_width, int n_thresholds,
                            const double* thresholds)
 {
@@ -1082,7 +1140,7 @@ const char* reed_last_error(reed_ctx* ctx) { return ctx ? ctx->err.c_str() : g_i
 void reed_destroy(reed_ctx* ctx)
 {
     if (!ctx) return;
-    void* ptrs[] = {ctx->d_pool, ctx->d_pool_state, ctx->d_hist, ctx->d_counters, ctx->d_splits, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
+    void* ptrs[] = {ctx->d_dsnap, ctx->d_pool, ctx->d_pool_state, ctx->d_hist, ctx->d_counters, ctx->d_splits, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
                     ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch,
                     ctx->d_thr, ctx->d_thr_hist, ctx->d_finished, ctx->d_damage, ctx->d_grads,
                     ctx->d_adj, ctx->d_kde};
@@ -1225,6 +1283,7 @@ int reed_cell_atoms(reed_ctx* ctx, uint64_t key, int32_t ix, int32_t iy, int32_t
     DevParams P;
     reed_run_opts o = diag_opts();
     make_params(ctx, P, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0, o);
+    set_feedback(ctx, P, ctx->d_damage);
     void* s = nullptr;
     int rc;
     if ((rc = scratch(ctx, 512, &s))) return rc;
@@ -1286,6 +1345,7 @@ int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double*
     DevParams P;
     reed_run_opts o = diag_opts();
     make_params(ctx, P, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0, o);
+    set_feedback(ctx, P, ctx->d_damage);
     const bool f64 = precision == REED_PREC_FP64;
     size_t smem = f64 ? reed_f64::smem_bytes(REED_TT_NONE, P.na, 0) : reed_f32::smem_bytes(REED_TT_NONE, P.na, 0);
     size_t bp = sizeof(double) * 3 * npts, ba = sizeof(int) * 3 * npts;

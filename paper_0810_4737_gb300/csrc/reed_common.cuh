@@ -67,6 +67,10 @@ struct DevParams {
     // lattice and window (Sec. 2 "Second")
     int kind, n, margin, nb, na, nspec, half_n;   // half_n = n / 2
     int g_nb, g_nbins;                             // neighbour-search grid: bins per axis, in all
+    // damage feedback: the cumulative map new cells read (null = off)
+    const double* fb_map;
+    int fb_n;
+    double fb_vox, fb_half, fb_dose, fb_atoms, fb_ec, sigma_am;
     double a, inv_a, sigma, anchor_shift;          // anchor_shift = 0.5 for even n
     double bas[REED_MAX_BASIS][3];
     int bspec[REED_MAX_BASIS];
@@ -253,6 +257,7 @@ __host__ __device__ __forceinline__ uint64_t clone_id(uint64_t parent, int level
 
 #define REED_TAG_CELL 1u
 #define REED_TAG_LAUNCH 2u
+#define REED_TAG_DAMAGE 3u
 
 __device__ __forceinline__ void draw4(uint64_t key, int ix, int iy, int iz, uint32_t word, uint32_t out[4])
 {

@@ -225,8 +225,31 @@ __device__ void make_atom(const DevParams& P, uint64_t key, int i, const int A[3
         p.w = R(REED_W_EMPTY);
         return;
     }
+    // damage feedback (reading of the paper's cumulative damage feedback):
+    // the cell is amorphous, with the wider offsets, with probability
+    // 1 - exp(-e / e_crit), e = dose * D / N for the map's voxel D holding
+    // the cell's centre and N lattice atoms per voxel
+    double sig = P.sigma;
+    if (P.fb_map) {
+        const double cc[3] = {(c[0] + 0.5) * P.a + P.fb_half, (c[1] + 0.5) * P.a + P.fb_half, (c[2] + 0.5) * P.a};
+        int vv[3];
+        bool in = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            vv[d] = (int)floor(cc[d] / P.fb_vox);
+            in = in && vv[d] >= 0 && vv[d] < P.fb_n;
+        }
+        if (in) {
+            const double D = P.fb_map[((size_t)vv[0] * P.fb_n + vv[1]) * P.fb_n + vv[2]];
+            const double e = P.fb_dose * D / P.fb_atoms;
+            const double pam = 1.0 - exp(-e / P.fb_ec);
+            uint32_t w[4];
+            draw4(key, c[0], c[1], c[2], REED_TAG_DAMAGE, w);
+            if (unit_open(w[0]) < pam) sig = P.sigma_am;
+        }
+    }
     double g[3] = {0.0, 0.0, 0.0};
-    if (P.sigma > 0.0) {
+    if (sig > 0.0) {
         uint32_t w[4];
         draw4(key, c[0], c[1], c[2], ((uint32_t)b << 4) | REED_TAG_CELL, w);
         if constexpr (sizeof(R) == 4) {
@@ -239,9 +262,9 @@ __device__ void make_atom(const DevParams& P, uint64_t key, int i, const int A[3
             box_muller3(w, g);
         }
     }
-    p.x = R(((double)(c[0] - A[0]) + P.bas[b][0]) * P.a + P.sigma * g[0]);
-    p.y = R(((double)(c[1] - A[1]) + P.bas[b][1]) * P.a + P.sigma * g[1]);
-    p.z = R(((double)(c[2] - A[2]) + P.bas[b][2]) * P.a + P.sigma * g[2]);
+    p.x = R(((double)(c[0] - A[0]) + P.bas[b][0]) * P.a + sig * g[0]);
+    p.y = R(((double)(c[1] - A[1]) + P.bas[b][1]) * P.a + sig * g[1]);
+    p.z = R(((double)(c[2] - A[2]) + P.bas[b][2]) * P.a + sig * g[2]);
     p.w = R(P.bspec[b] + (active ? 0 : 2));
 }
 

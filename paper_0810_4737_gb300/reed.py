@@ -94,7 +94,8 @@ class reed_stats_t(C.Structure):
 EXPORTED = ["reed_init", "reed_run", "reed_range_profile", "reed_stats", "reed_track_records", "reed_trace",
             "reed_reset", "reed_last_error", "reed_destroy", "reed_philox", "reed_cell_atoms", "reed_forces",
             "reed_window_replay", "reed_run_static", "reed_thresholds", "reed_damage_map", "reed_track_grads",
-            "reed_kde_profile", "reed_grad", "reed_set_theta", "reed_update_thresholds", "reed_get_thresholds", "reed_peaks", "reed_autotune"]
+            "reed_kde_profile", "reed_grad", "reed_set_theta", "reed_update_thresholds", "reed_get_thresholds", "reed_peaks", "reed_autotune",
+            "reed_set_damage_feedback", "reed_set_damage_map"]
 
 _LIB = None
 _D = C.POINTER(C.c_double)
@@ -139,6 +140,8 @@ def lib():
         L.reed_update_thresholds.argtypes = [vp, vp, C.c_int, C.c_double, C.c_int, _D]
         L.reed_get_thresholds.argtypes = [vp, vp]
         L.reed_peaks.argtypes = [C.POINTER(reed_peaks_t)]
+        L.reed_set_damage_feedback.argtypes = [vp, C.c_double, C.c_double, C.c_double]
+        L.reed_set_damage_map.argtypes = [vp, vp, C.c_int, C.c_double]
         L.reed_autotune.argtypes = [vp] + [C.c_double] * 6 + [C.c_int64, C.c_uint64, C.POINTER(reed_run_opts),
                                                               C.POINTER(reed_tune_entry), C.c_int, _I32]
         L.reed_last_error.argtypes = [vp]
@@ -338,6 +341,21 @@ def reed_get_thresholds(ctx):
     return out
 
 
+def reed_set_damage_feedback(ctx, dose_scale, e_crit, sigma_amorphous):
+    _check(lib().reed_set_damage_feedback(ctx, dose_scale, e_crit, sigma_amorphous), ctx)
+
+
+def reed_set_damage_map(ctx, damage_map, voxel):
+    """damage_map: n^3 voxels + overflow (as reed_damage_map returns them),
+    a flat array, an (n, n, n) array plus an overflow, or a device address."""
+    if isinstance(damage_map, int):
+        raise ValueError("give the voxel count with a device address: use lib().reed_set_damage_map")
+    a = np.ascontiguousarray(damage_map, dtype=np.float64).ravel()
+    n = int(round((a.size - 1) ** (1.0 / 3.0)))
+    assert n ** 3 + 1 == a.size, "expected n^3 voxels and the overflow"
+    _check(lib().reed_set_damage_map(ctx, a.ctypes.data, n, voxel), ctx)
+
+
 def reed_peaks() -> dict:
     """Measured FP32/FP64/SFU/shared-memory throughput of the current GPU."""
     p = reed_peaks_t()
@@ -419,6 +437,9 @@ class Reed:
         self.w = w
         self._sp = species_array(w)
         self.ctx = reed_init(lattice_struct(w), self._sp, len(w["species"]), potentials_struct(w))
+        if float(w.get("e_crit", 0.0)) > 0.0:
+            reed_set_damage_feedback(self.ctx, float(w.get("dose_scale", 0.0)), float(w["e_crit"]),
+                                     float(w.get("sigma_amorphous", 0.0)))
 
     def run(self, n_ions=None, seed=None, precision=PREC_MIXED, tolerate=(), **kw):
         """Run primaries; anomaly codes listed in `tolerate` (e.g. E_NEIGHBOR)
@@ -466,6 +487,9 @@ class Reed:
 
     def damage_map(self):
         return reed_damage_map(self.ctx, int(self.w["damage_n"]))
+
+    def set_damage_map(self, damage_map, voxel=None):
+        reed_set_damage_map(self.ctx, damage_map, float(self.w.get("damage_voxel", 10.0)) if voxel is None else voxel)
 
     def track_grads(self):
         return reed_track_grads(self.ctx)

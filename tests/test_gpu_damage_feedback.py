@@ -114,7 +114,7 @@ def test_second_run_reads_the_first_runs_damage(R):
     out = []
     for _ in range(2):
         with R.Reed(w) as ctx:
-            ctx.run(n_ions=n, seed=5)
+            ctx.run(n_ions=n, seed=5, record_capacity=4 * n)   # room for both runs' records
             r1 = ctx.records()
             ctx.run(n_ions=n, seed=5, first_id=n)
             r2 = ctx.records()[len(r1):]

@@ -132,7 +132,9 @@ typedef struct {
     int32_t trace_tracks;      /* record the first trace_steps steps of primaries */
     int32_t trace_steps;       /*   first_id .. first_id + trace_tracks - 1 */
     int32_t reserved;
-    int64_t record_capacity;   /* records kept (further tracks are counted only) */
+    int64_t record_capacity;   /* records kept (further tracks are counted only); fixed by the
+                                  first run that keeps records after init/reset (0 = n_ions x
+                                  (1 + 4 n_thresholds) + 1024 of that run) */
     void* stream;              /* cudaStream_t to run on; NULL = default stream */
     /* Adaptive cloning depths (Sec. 2; re-estimated from finished ions, Sec. 3):
      * with adaptive = 1 the first n_initial primaries run without enhancement,

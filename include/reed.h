@@ -185,6 +185,10 @@ typedef struct {
      * particle's kinetic energy changes by much more than de_max (eV) in one
      * step.  0 = off. */
     double de_max;
+    /* Polls of the shared clone pool by a CTA that ran out of work before it
+     * gives up and the run returns REED_E_TIMEOUT (each poll sleeps about
+     * 0.5-4 us); 0 = 2^26, about five minutes. */
+    int64_t pool_poll_limit;
 } reed_run_opts;
 
 /* Per-track result: the depth and weight of one finished track (Sec. 3, result messages). */

@@ -347,6 +347,7 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.dhalf = 0.5 * P.dn * P.dvox;
     P.dmin = o.damage_min;
     P.de_max = o.de_max > 0.0 ? o.de_max : 0.0;
+    P.pool_polls = o.pool_poll_limit > 0 ? o.pool_poll_limit : (1ll << 26);
     const double skin = o.nl_skin > 0.0 ? o.nl_skin : kSkin;
     // neighbour-search grid over the window: bins no narrower than the list
     // radius (with a margin for rounding), at most 10 per axis

@@ -96,6 +96,7 @@ struct DevParams {
     // integrator (Sec. 2, Fig. "dt_E")
     double dt_max, dx_max, e_stop, de_max;
     long long step_cap;
+    long long pool_polls;   // polls of the clone pool by an idle CTA before it gives up
     // beam
     double v0, tilt, rot_lo, rot_span, cos_tmax;
     int beam_mode;

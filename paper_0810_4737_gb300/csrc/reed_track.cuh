@@ -32,9 +32,7 @@
 
 enum { SRC_NONE = 0, SRC_PRIMARY = 1, SRC_CLONE = 2, SRC_STOLEN = 3 };
 enum { POOL_EMPTY = 0, POOL_WRITING = 1, POOL_FULL = 2, POOL_READING = 3 };
-// polls of the clone pool by an idle CTA before it gives up (each sleeps up
-// to 4 us: about five minutes in all)
-#define REED_POOL_POLLS (1ll << 26)
+
 enum { EV_NONE = 0, EV_END = 1, EV_CLONE = 2, EV_CKPT = 3 };
 
 // Ion state as stored in shared memory and in clone records.  Position,
@@ -1207,7 +1205,7 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                     }
                     if (*(volatile unsigned*)&B.pool_ctl[0] >= gridDim.x && *(volatile unsigned*)&B.pool_ctl[1] == 0u)
                         break;
-                    if (it >= REED_POOL_POLLS) {
+                    if (it >= P.pool_polls) {
                         atomicOr(B.status, ERR_TIMEOUT);
                         break;
                     }

@@ -54,7 +54,7 @@ class reed_run_opts(C.Structure):
                 ("damage_n", C.c_int32), ("reserved3", C.c_int32), ("damage_voxel", C.c_double),
                 ("damage_min", C.c_double), ("adjoint", C.c_int32), ("adj_segment", C.c_int32),
                 ("adj_every", C.c_int32), ("reserved4", C.c_int32),
-                ("nl_skin", C.c_double), ("de_max", C.c_double)]
+                ("nl_skin", C.c_double), ("de_max", C.c_double), ("pool_poll_limit", C.c_int64)]
 
 
 class reed_track_record(C.Structure):
@@ -203,7 +203,7 @@ def potentials_struct(w) -> reed_potentials:
 def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, record=True, record_capacity=0,
              trace_tracks=0, trace_steps=0, stream=None, adaptive=False, epoch_size=4096, n_initial=50,
              target_tracks=0, damage=True, adjoint=False, adj_segment=200, adj_every=20, nl_skin=0.0,
-             device_thresholds=False, thresholds=None) -> reed_run_opts:
+             device_thresholds=False, thresholds=None, pool_poll_limit=0) -> reed_run_opts:
     o = reed_run_opts()
     o.dt_max_fs, o.dx_max, o.e_stop = w["dt_max_fs"], w["dx_max"], w["e_stop"]
     o.step_cap = int(w["step_cap"])
@@ -228,6 +228,7 @@ def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, reco
     o.adjoint, o.adj_segment, o.adj_every = (1 if adjoint else 0), adj_segment, adj_every
     o.nl_skin = nl_skin
     o.de_max = float(w.get("de_max", 0.0))
+    o.pool_poll_limit = pool_poll_limit
     return o
 
 

@@ -264,14 +264,16 @@ def test_limits_and_errors(R):
         ctx.run(n_ions=64, seed=1)
         st = ctx.stats()
         assert st["tracks"] == 64 and st["failed"] == 0
-    # a 6^3-cell Tersoff window (1728 atoms) needs more shared memory than a
-    # CTA can have, in either form: refused up front
+    # a 6^3-cell Tersoff window (1728 atoms) fits one CTA in the mixed form;
+    # in FP64 it needs more shared memory than a CTA can have: refused up front
     wt = workload("as10kev_si_300k_tersoff", n=6)
     with R.Reed(wt) as ctx:
-        for prec in (0, 1):
-            with pytest.raises(R.ReedError) as e:
-                ctx.run(n_ions=1, precision=prec)
-            assert e.value.code == R.E_SMEM
+        with pytest.raises(R.ReedError) as e:
+            ctx.run(n_ions=1, precision=1)
+        assert e.value.code == R.E_SMEM
+        ctx.run(n_ions=2, seed=1, step_cap=300, tolerate=(R.W_NEIGHBOR,))
+        st = ctx.stats()
+        assert st["tracks"] == 2 and st["failed"] == 0
     w = workload("b1kev_si_0k_zbl")
     with R.Reed(w) as ctx:
         with pytest.raises(R.ReedError) as e:

@@ -727,6 +727,43 @@ struct WorkCount {
 // Writes W.frc of every present atom.  With target-target terms the
 // integrated atoms are visited through their list slots (balanced across
 // threads); the others only contribute ion-target pairs.
+// The ion-target part of one atom's force pass at its current position p,
+// and (integrated atoms) the second half kick: the arithmetic of atom_force
+// for an atom without target-target terms, on values held in registers.
+template <typename R>
+__device__ __forceinline__ void ion_atom_step(const DevParams& P, const HotParams<R>& H, const TrackShared<R>* S,
+                                              const V4<R>& p, V4<R>& v, bool act, R hdt, V4<R>& f, Partial<R>& out)
+{
+    R fx = R(0), fy = R(0), fz = R(0);
+    const R dx = p.x - S->rel[0], dy = p.y - S->rel[1], dz = p.z - S->rel[2];
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 < H.rc2) {
+        R U, rw;
+        const R g = ion_pair<R>(H, P.spline_on, P.rho_on, species_of(p), r2, U, rw);
+        fx -= g * dx;
+        fy -= g * dy;
+        fz -= g * dz;
+        out.fx += g * dx;
+        out.fy += g * dy;
+        out.fz += g * dz;
+        out.rho += rw;
+        out.epot += U;
+        out.pairs += 1;
+    }
+    f.x = fx;
+    f.y = fy;
+    f.z = fz;
+    f.w = R(0);
+    if (act) {
+        const R kk = hdt * H.invM2[species_of(p)];
+        v.x += kk * fx;
+        v.y += kk * fy;
+        v.z += kk * fz;
+        out.vmax2 = max(out.vmax2, v.x * v.x + v.y * v.y + v.z * v.z);
+        if (H.de_max > R(0)) out.pmax = max(out.pmax, fabs(fx * v.x + fy * v.y + fz * v.z));
+    }
+}
+
 template <typename R, int TT, bool KICK>
 __device__ __forceinline__ void atom_force(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int i, int k,
                                            R hdt, Partial<R>& out, bool want_energy)
@@ -1293,6 +1330,46 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
             const R dt = R(S->dt), hdt = R(0.5) * R(S->dt);
             const int shift = S->shift;
             const uint64_t key = S->ion.key;
+            Partial<R> q = {R(0), R(0), R(0), R(0), R(0), R(0), 0, 0};
+            if constexpr (TT == REED_TT_NONE) {
+                // no target-target forces: each atom's whole step (re-anchor,
+                // half kick, drift, ion-target force, half kick) in one pass
+                // with the same arithmetic as the separate phases
+                for (int i = tid; i < P.na; i += blockDim.x) {
+                    V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
+                    if (shift) {
+                        const V4<R> p0 = p, v0 = v;
+                        if (reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f))
+                            deposit_damage<R>(P, B, p0, v0, S->Aold, ldexp(1.0, -S->ion.level));
+                    }
+                    if (!is_present(p)) {
+                        if (shift) {
+                            W.pos[i] = p;
+                            W.vel[i] = v;
+                            W.frc[i] = f;
+                        }
+                        continue;
+                    }
+                    const bool act = is_active(p);
+                    if (act) {
+                        ++wc.moved;
+                        const R k = hdt * H.invM2[species_of(p)];
+                        v.x += k * f.x;
+                        v.y += k * f.y;
+                        v.z += k * f.z;
+                        p.x += dt * v.x;
+                        p.y += dt * v.y;
+                        p.z += dt * v.z;
+                    }
+                    ion_atom_step<R>(P, H, W.S, p, v, act, hdt, f, q);
+                    W.pos[i] = p;
+                    W.vel[i] = v;
+                    W.frc[i] = f;
+                }
+                reduce_partials<R, TT>(W, q);
+                __syncthreads();
+                lap(PH_FORCE);
+            } else {
             // phase A: re-anchor and first half kick + drift of own atoms
             bool any_new = false;
             R pm1 = R(0), pm2 = R(0);   // this thread's two longest paths
@@ -1362,11 +1439,11 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                     lap(PH_PASS1);
                 }
             }
-            Partial<R> q = {R(0), R(0), R(0), R(0), R(0), R(0), 0, 0};
             force_phase<R, TT, true>(P, H, W, hdt, q, false);
             reduce_partials<R, TT>(W, q);
             __syncthreads();
             lap(PH_FORCE);
+            }
             if (tid == 0) {
                 R red[REED_NRED];
                 gather_partials<R, TT>(W, red);

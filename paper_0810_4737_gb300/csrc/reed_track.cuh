@@ -728,7 +728,7 @@ struct WorkCount {
 // integrated atoms are visited through their list slots (balanced across
 // threads); the others only contribute ion-target pairs.
 // The ion-target part of one atom's force pass at its current position p,
-// and (integrated atoms) the second half kick: the arithmetic of atom_force
+// and (integrated atoms) the second half kick: the operations of atom_force
 // for an atom without target-target terms, on values held in registers.
 template <typename R>
 __device__ __forceinline__ void ion_atom_step(const DevParams& P, const HotParams<R>& H, const TrackShared<R>* S,
@@ -1333,8 +1333,8 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
             Partial<R> q = {R(0), R(0), R(0), R(0), R(0), R(0), 0, 0};
             if constexpr (TT == REED_TT_NONE) {
                 // no target-target forces: each atom's whole step (re-anchor,
-                // half kick, drift, ion-target force, half kick) in one pass
-                // with the same arithmetic as the separate phases
+                // half kick, drift, ion-target force, half kick) in one pass,
+                // the same operations as the separate phases of the other models
                 for (int i = tid; i < P.na; i += blockDim.x) {
                     V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
                     if (shift) {

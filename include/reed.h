@@ -176,7 +176,8 @@ typedef struct {
     int32_t reserved4;
     /* Target neighbour lists (Tersoff, Buckingham): list radius = cutoff +
      * nl_skin; a list is rebuilt after a window move and when the two longest
-     * atom paths since the last build add up to more than nl_skin.  0 = 0.3 A. */
+     * atom paths since the last build add up to more than nl_skin.  0 = 0.2 A
+     * for Tersoff, 0.3 A for the pair lists. */
     double nl_skin;
     /* Energy term of the adaptive step (the paper's step rule in terms of the
      * kinetic and collisional energy, Sec. 2): when > 0, also

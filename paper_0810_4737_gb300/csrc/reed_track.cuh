@@ -65,7 +65,7 @@ template <typename R> struct TrackShared {
     double gth[8];
     R adj_red[REED_MAX_WARPS][12];
     int Aold[3];
-    int shift, rebuild, event, status, src, top, nclone, slot;
+    int shift, event, status, src, top, nclone, slot;
     int need_count, active_count;
     int scan[2][REED_MAX_WARPS];
     long long pidx;
@@ -1209,7 +1209,6 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
     for (;;) {
         // ---- acquire a track: own clone stack first, then a new primary
         if (tid == 0) {
-            S->rebuild = 0;
             S->nthr = P.nthr;
             for (int k = 0; k < P.nthr; ++k) S->thr[k] = P.thr_from_device ? B.thr[k] : P.thr[k];
             if (S->top > 0) {
@@ -1371,16 +1370,13 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                 lap(PH_FORCE);
             } else {
             // phase A: re-anchor and first half kick + drift of own atoms
-            bool any_new = false;
             R pm1 = R(0), pm2 = R(0);   // this thread's two longest paths
             for (int i = tid; i < P.na; i += blockDim.x) {
                 V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
                 if (shift) {
                     const V4<R> p0 = p, v0 = v;
-                    if (reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f)) {
-                        any_new = true;
+                    if (reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f))
                         deposit_damage<R>(P, B, p0, v0, S->Aold, ldexp(1.0, -S->ion.level));
-                    }
                 }
                 if (is_active(p)) {
                     ++wc.moved;
@@ -1406,7 +1402,6 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                 W.vel[i] = v;
                 if (shift) W.frc[i] = f;
             }
-            (void)any_new;
             if constexpr (TT != REED_TT_NONE) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {

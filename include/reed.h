@@ -247,10 +247,15 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
  * defaults: 0.1 fs, 0.05 A, 5 eV, 2e6 steps, mixed precision, no cloning,
  * 100 bins of 10 A).  With record_tracks and record_capacity 0 the record
  * buffer holds n_ions * (1 + 4 n_thresholds) + 1024 records.
+ * Clones are run depth first by the CTA that made them, or, while some CTA
+ * is out of work, donated to a shared pool that idle CTAs take from (the
+ * paper's host handing returned clones to free clients, Sec. 3).
  * Returns REED_OK, REED_W_NEIGHBOR (completed; see nb_overflow), or an error:
  * REED_E_ARG, REED_E_SMEM, REED_E_CUDA, REED_E_NOMEM; REED_E_QUEUE_FULL and
  * REED_E_NONFINITE mean the run completed but clones or tracks were lost
- * (counted in reed_stats). */
+ * (counted in reed_stats); REED_E_TIMEOUT means a CTA out of work stopped
+ * polling the clone pool after opt->pool_poll_limit polls (donated clones may
+ * be missing). */
 int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double tilt_deg,
              double rot_deg_lo, double rot_deg_hi, int64_t n_ions, uint64_t seed,
              const reed_run_opts* opt);
@@ -392,7 +397,9 @@ typedef struct {
 
 int reed_peaks(reed_peaks_t* out);
 
-/* Zero all tallies, records and counters. */
+/* Zero all tallies, records and counters; drop the damage map and the
+ * sensitivities (cloning depths, damage-feedback settings and autotuned
+ * launch shapes are kept). */
 int reed_reset(reed_ctx* ctx);
 
 /* Message of the last failure of this context (ctx == NULL: of the last

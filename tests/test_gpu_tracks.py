@@ -287,3 +287,24 @@ def test_limits_and_errors(R):
         assert e.value.code == R.E_ARG
         ctx.run(n_ions=4, seed=1)                   # still usable
         assert ctx.stats()["tracks"] == 4
+
+
+def test_degenerate_beams(R, O):
+    """An ion launched below the stopping energy stops at once above the
+    surface; a grazing ion (tilt 90 deg) never enters and runs into the step
+    cap; both exactly as in the oracle."""
+    w = workload("b1kev_si_0k_zbl", energy=3.0)
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=37, seed=1)
+        bins, extra = ctx.profile()
+        st = ctx.stats()
+    ref = O.run(O.params(w), 37, seed=1)
+    assert st["stopped"] == 37 and st["steps"] == ref["steps"] == 37
+    assert extra[0] == ref["under"] == 37 and bins.sum() == 0
+    w = workload("b1kev_si_0k_zbl", tilt=90.0, step_cap=500)
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=19, seed=2)
+        st = ctx.stats()
+    ref = O.run(O.params(w), 19, seed=2)
+    assert st["truncated"] == 19 and st["w_trunc"] == ref["w_trunc"] == 19
+    assert st["steps"] == ref["steps"] == 19 * 500

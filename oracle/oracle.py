@@ -42,6 +42,7 @@ class Params(C.Structure):
     _fields_ = [
         ("Z1", C.c_double), ("M1", C.c_double),
         ("lattice", C.c_int), ("n", C.c_int), ("margin", C.c_int), ("nspec", C.c_int),
+        ("target", C.c_int),
         ("a", C.c_double), ("sigma", C.c_double),
         ("Z2", C.c_double * 2), ("M2", C.c_double * 2),
         ("rc", C.c_double), ("rt", C.c_double),
@@ -182,7 +183,8 @@ def params(w: dict, screening: int = 1) -> Params:
     p.E0 = w["energy"]
     p.tilt = w["tilt"]
     p.rot_lo, p.rot_hi = w["rot"]
-    p.beam_mode = 1 if w["beam_mode"] == "cone" else 0
+    p.beam_mode = {"fixed": 0, "cone": 1, "recoil": 2}[w["beam_mode"]]
+    p.target = {"surface": 0, "bulk": 1}[w.get("target", "surface")]
     thr = list(w["thresholds"])
     assert len(thr) <= 16
     p.nthr = len(thr)

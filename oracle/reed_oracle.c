@@ -63,6 +63,10 @@ typedef struct {
     int n;            /* cells per window edge */
     int margin;       /* frozen outer cell layers (0 or 1) */
     int nspec;
+    /* target geometry: 0 = surface (target z >= 0, (001) surface), 1 = bulk
+     * (infinite crystal; the recoil's own site, basis atom 0 of cell
+     * (0,0,0), is vacant) */
+    int target;
     double a;         /* lattice constant, A */
     double sigma;     /* thermal displacement per Cartesian coordinate, A */
     double Z2[2], M2[2];
@@ -86,14 +90,16 @@ typedef struct {
     int64_t step_cap;
     /* beam */
     double E0, tilt, rot_lo, rot_hi;  /* eV, degrees */
-    int beam_mode;    /* 0: fixed tilt, rotation U[lo,hi); 1: cone of half-angle tilt */
+    int beam_mode;    /* 0: fixed tilt, rotation U[lo,hi); 1: cone of half-angle tilt;
+                         2: recoil from the origin site, direction uniform on the sphere */
     /* cloning depths and histogram */
     int nthr;
     double thr[16];
     int nbins;
     double bin_w;
     /* cumulative damage map (reading): dn^3 voxels of dvox A, origin
-     * (-dn dvox / 2, -dn dvox / 2, 0); atoms with KE > dmin deposit w KE */
+     * (-dn dvox / 2, -dn dvox / 2, 0) -- in a bulk target (-dn dvox / 2) on
+     * all three axes; atoms with KE > dmin deposit w KE */
     int dn;
     double dvox, dmin;
     /* energy term of the adaptive step (eV per step; 0 = off) */
@@ -207,8 +213,9 @@ static double o_cell_sigma(const o_params* P, uint64_t key, int32_t ix, int32_t 
 {
     if (!(P->fb_ec > 0.0) || !P->fb_map || P->dn <= 0) return P->sigma;
     double half = 0.5 * P->dn * P->dvox;
+    double zhalf = P->target == 1 ? half : 0.0;
     int v[3];
-    double c[3] = {(ix + 0.5) * P->a + half, (iy + 0.5) * P->a + half, (iz + 0.5) * P->a};
+    double c[3] = {(ix + 0.5) * P->a + half, (iy + 0.5) * P->a + half, (iz + 0.5) * P->a + zhalf};
     for (int d = 0; d < 3; ++d) {
         v[d] = (int)floor(c[d] / P->dvox);
         if (v[d] < 0 || v[d] >= P->dn) return P->sigma;
@@ -225,27 +232,40 @@ static double o_cell_sigma(const o_params* P, uint64_t key, int32_t ix, int32_t 
 
 /* Atoms of absolute cell (ix,iy,iz), absolute coordinates.  Cells with
  * iz < 0 lie above the surface and are empty (target occupies z >= 0).
- * Returns the number of atoms written. */
-int o_cell_atoms(const o_params* P, uint64_t key, int32_t ix, int32_t iy, int32_t iz,
-                 double* xyz, int* sp)
+ * reading (the paper's UO2 runs start from a lattice site, Sec. 4.1): a bulk
+ * target fills space, and the site the recoil starts from -- basis atom 0 of
+ * cell (0,0,0) -- is empty in every realisation of that cell.
+ * Returns the number of atoms written; bas (may be NULL) receives each
+ * atom's basis index. */
+static int o_cell_atoms_b(const o_params* P, uint64_t key, int32_t ix, int32_t iy, int32_t iz,
+                          double* xyz, int* sp, int* bas)
 {
-    if (iz < 0) return 0;
+    if (P->target != 1 && iz < 0) return 0;
     int nb = o_basis_count(P->lattice);
     const double(*B)[3] = P->lattice == 1 ? O_FLUORITE : O_DIAMOND;
     double sig = o_cell_sigma(P, key, ix, iy, iz);
+    int m = 0;
     for (int b = 0; b < nb; ++b) {
+        if (P->target == 1 && b == 0 && ix == 0 && iy == 0 && iz == 0) continue;   /* the recoil's site */
         double g[3] = {0.0, 0.0, 0.0};
         if (sig > 0.0) {
             uint32_t w[4];
             o_draw(key, ix, iy, iz, ((uint32_t)b << 4) | O_TAG_CELL, w);
             o_gauss3(w, g);
         }
-        xyz[3 * b + 0] = (ix + B[b][0]) * P->a + sig * g[0];
-        xyz[3 * b + 1] = (iy + B[b][1]) * P->a + sig * g[1];
-        xyz[3 * b + 2] = (iz + B[b][2]) * P->a + sig * g[2];
-        sp[b] = o_basis_species(P->lattice, b);
+        xyz[3 * m + 0] = (ix + B[b][0]) * P->a + sig * g[0];
+        xyz[3 * m + 1] = (iy + B[b][1]) * P->a + sig * g[1];
+        xyz[3 * m + 2] = (iz + B[b][2]) * P->a + sig * g[2];
+        sp[m] = o_basis_species(P->lattice, b);
+        if (bas) bas[m] = b;
+        ++m;
     }
-    return nb;
+    return m;
+}
+
+int o_cell_atoms(const o_params* P, uint64_t key, int32_t ix, int32_t iy, int32_t iz, double* xyz, int* sp)
+{
+    return o_cell_atoms_b(P, key, ix, iy, iz, xyz, sp, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -400,9 +420,10 @@ static void o_deposit(const o_params* P, o_tally* T, const double* x, const doub
         return;
     }
     double half = 0.5 * P->dn * P->dvox;
+    double zhalf = P->target == 1 ? half : 0.0;
     int ix = (int)floor((x[0] + half) / P->dvox);
     int iy = (int)floor((x[1] + half) / P->dvox);
-    int iz = (int)floor(x[2] / P->dvox);
+    int iz = (int)floor((x[2] + zhalf) / P->dvox);
     size_t n = (size_t)P->dn;
     if (ix < 0 || iy < 0 || iz < 0 || ix >= P->dn || iy >= P->dn || iz >= P->dn)
         T->damage[n * n * n] += w * ke;
@@ -499,8 +520,8 @@ static int o_in_window(const o_params* P, const int A[3], const int c[3])
 static void o_add_cell(const o_params* P, o_win* W, uint64_t key, const int c[3])
 {
     double xyz[36];
-    int sp[12];
-    int m = o_cell_atoms(P, key, c[0], c[1], c[2], xyz, sp);
+    int sp[12], bas[12];
+    int m = o_cell_atoms_b(P, key, c[0], c[1], c[2], xyz, sp, bas);
     for (int b = 0; b < m; ++b) {
         int j = W->n++;
         for (int d = 0; d < 3; ++d) {
@@ -510,7 +531,7 @@ static void o_add_cell(const o_params* P, o_win* W, uint64_t key, const int c[3]
             W->cell[3 * j + d] = c[d];
         }
         W->sp[j] = sp[b];
-        W->bas[j] = b;
+        W->bas[j] = bas[b];
         W->act[j] = 1;
     }
 }
@@ -752,7 +773,7 @@ static void o_drag(const o_params* P, double gam, double rho0, const o_ion* I, c
                    const double* x, double rho, double F[3])
 {
     double fl = 1.0 + P->s_loc * (rho / rho0 - 1.0);
-    double g = (x[2] >= 0.0) ? gam * fl : 0.0;
+    double g = (P->target == 1 || x[2] >= 0.0) ? gam * fl : 0.0;   /* inside the target */
     for (int d = 0; d < 3; ++d) F[d] = -g * v[d];
     (void)I;
 }
@@ -833,7 +854,10 @@ static double o_step(const o_params* P, const o_consts* K, o_ion* I, o_win* W, u
 
 /* ------------------------------------------------------------------------ */
 /* Track launch (beam) -- reading: ion at z = -rc, lateral position uniform */
-/* in the surface cell at (0,0), direction from tilt and rotation.           */
+/* in the surface cell at (0,0), direction from tilt and rotation.  Recoil  */
+/* (the paper's on-lattice ions with random direction, Sec. 4.1): the ion    */
+/* starts on the site of basis atom 0 of cell (0,0,0) of a bulk target with */
+/* a direction uniform over the sphere.                                     */
 /* ------------------------------------------------------------------------ */
 static void o_launch(const o_params* P, uint64_t seed, uint64_t id, o_ion* I)
 {
@@ -849,14 +873,23 @@ static void o_launch(const o_params* P, uint64_t seed, uint64_t id, o_ion* I)
         double ct = 1.0 - o_unit(w[2]) * (1.0 - cmax);
         th = acos(ct);
         ph = 2.0 * O_PI * o_unit(w[3]);
+    } else if (P->beam_mode == 2) {
+        /* uniform on the unit sphere: cos(theta) uniform in (-1, 1) */
+        th = acos(1.0 - 2.0 * o_unit(w[2]));
+        ph = 2.0 * O_PI * o_unit(w[3]);
     } else {
         th = P->tilt * O_PI / 180.0;
         ph = (P->rot_lo + (P->rot_hi - P->rot_lo) * o_unit(w[2])) * O_PI / 180.0;
     }
     double sp = sqrt(2.0 * P->E0 / P->M1);
-    I->x[0] = P->a * o_unit(w[0]);
-    I->x[1] = P->a * o_unit(w[1]);
-    I->x[2] = -P->rc;
+    if (P->beam_mode == 2) {
+        const double(*B)[3] = P->lattice == 1 ? O_FLUORITE : O_DIAMOND;
+        for (int d = 0; d < 3; ++d) I->x[d] = B[0][d] * P->a;
+    } else {
+        I->x[0] = P->a * o_unit(w[0]);
+        I->x[1] = P->a * o_unit(w[1]);
+        I->x[2] = -P->rc;
+    }
     I->v[0] = sp * sin(th) * cos(ph);
     I->v[1] = sp * sin(th) * sin(ph);
     I->v[2] = sp * cos(th);
@@ -879,11 +912,20 @@ static int o_window_capacity(const o_params* P)
 /* ------------------------------------------------------------------------ */
 /* Tallies                                                                  */
 /* ------------------------------------------------------------------------ */
+/* Depth of a track for the range tally and the cloning depths: z below the
+ * surface; in a bulk target (reading) the distance from the starting site,
+ * the range of the paper's recoil runs (Sec. 4.1). */
+static double o_depth(const o_params* P, const o_ion* I)
+{
+    if (P->target != 1) return I->x[2];
+    return sqrt(I->x[0] * I->x[0] + I->x[1] * I->x[1] + I->x[2] * I->x[2]);
+}
+
 static void o_tally_finish(const o_params* P, o_tally* T, const o_ion* I, int status)
 {
     double w = ldexp(1.0, -I->level);
     if (status == O_STOPPED) {
-        double z = I->x[2];
+        double z = o_depth(P, I);
         if (z < 0.0) T->hist[P->nbins] += w;
         else {
             double q = floor(z / P->bin_w);
@@ -903,7 +945,7 @@ static int o_check(const o_params* P, const o_ion* I)
 {
     double E = 0.5 * P->M1 * (I->v[0] * I->v[0] + I->v[1] * I->v[1] + I->v[2] * I->v[2]);
     if (E < P->e_stop) return O_STOPPED;
-    if (I->x[2] < -P->rc && I->v[2] < 0.0) return O_BACK;
+    if (P->target != 1 && I->x[2] < -P->rc && I->v[2] < 0.0) return O_BACK;
     if (I->steps >= P->step_cap) return O_TRUNC;
     return O_ALIVE;
 }
@@ -952,7 +994,7 @@ static int o_run_lineage(const o_params* P, const o_consts* K, uint64_t seed, ui
             T->steps += 1;
             st = o_check(P, &I);
             if (st != O_ALIVE) break;
-            while (I.level < P->nthr && I.x[2] >= P->thr[I.level]) {
+            while (I.level < P->nthr && o_depth(P, &I) >= P->thr[I.level]) {
                 /* clone: copy of the current state, half weight each */
                 I.level += 1;
                 o_snap* S = &stack[top++];
@@ -968,7 +1010,7 @@ static int o_run_lineage(const o_params* P, const o_consts* K, uint64_t seed, ui
             if (W.act[j]) o_deposit(P, T, &W.x[3 * j], &W.v[3 * j], P->M2[W.sp[j]], ldexp(1.0, -I.level));
         if (recs) {
             o_record R;
-            R.id = I.id; R.primary = I.primary; R.z = I.x[2]; R.t = I.t;
+            R.id = I.id; R.primary = I.primary; R.z = o_depth(P, &I); R.t = I.t;
             R.steps = I.steps; R.level = I.level; R.status = st;
             o_recbuf_push(recs, &R);
         }

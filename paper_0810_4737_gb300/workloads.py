@@ -22,6 +22,18 @@ The five workloads follow the synthetic cases of the REED-MD study:
     directions within 10 deg of [001], 64^3 damage voxels;
   * ``b10kev_si_300k_adjoint`` -- 16384 B ions, 10 keV, Si at 300 K, kernel-
     density depth profile (1 nm width, 200 bins) for the adjoint.
+
+and the two actinide-oxide runs of the paper itself (Sec. 4.1, 4.2): ions
+starting on a lattice site of bulk fluorite UO2 in a random direction, a
+window of 27 cells of 12 atoms with the ion's cell in the centre, ZBL forces
+only (Sec. 2 "First"), eight adaptive cloning distances, ranges measured from
+the starting site:
+  * ``u85kev_uo2_300k_recoil`` -- 5120 U-235 recoils of 85 keV (the recoil
+    of a Pu-239 alpha decay), 200 bins of 5 A;
+  * ``kr85mev_uo2_300k_recoil`` -- 1024 Kr fission fragments of 85 MeV,
+    400 bins of 250 A (ranges of several micrometres).
+The thermal displacement of the UO2 lattice comes from MD data the paper
+cites but does not give; these workloads use the 0.076 A of the others.
 """
 from __future__ import annotations
 
@@ -34,6 +46,9 @@ AR40 = {"Z": 18.0, "M": 39.948}
 SI = {"Z": 14.0, "M": 28.0855}
 CE = {"Z": 58.0, "M": 140.116}
 O16 = {"Z": 8.0, "M": 15.999}
+U235 = {"Z": 92.0, "M": 235.043930}
+U = {"Z": 92.0, "M": 238.02891}
+KR = {"Z": 36.0, "M": 83.798}
 
 # Tersoff Si(C) parameter set, Phys. Rev. B 38, 9902 (1988).
 TERSOFF_SI_C = {
@@ -54,6 +69,7 @@ BUCKINGHAM_CEO2 = {
 
 _BASE = {
     "lattice": "diamond",
+    "target": "surface",    # "surface": z >= 0 with a (001) surface; "bulk": infinite, recoil beam
     "a": 5.431,
     "n": 3,
     "margin": 0,
@@ -108,6 +124,14 @@ WORKLOADS = {
     "b10kev_si_300k_adjoint": dict(
         _BASE, ion=B11, energy=10000.0, n_ions=16384, sigma=0.076, rot=(0.0, 45.0),
         n_bins=200, bin_w=10.0),
+    "u85kev_uo2_300k_recoil": dict(
+        _BASE, ion=U235, energy=85000.0, n_ions=5120, lattice="fluorite", a=5.4704, n=3,
+        sigma=0.076, species=[U, O16], target="bulk", beam_mode="recoil",
+        thresholds=_geom(100.0, 800.0, 8), n_bins=200, bin_w=5.0),
+    "kr85mev_uo2_300k_recoil": dict(
+        _BASE, ion=KR, energy=85.0e6, n_ions=1024, lattice="fluorite", a=5.4704, n=3,
+        sigma=0.076, species=[U, O16], target="bulk", beam_mode="recoil", step_cap=10_000_000,
+        thresholds=_geom(2000.0, 60000.0, 8), n_bins=400, bin_w=250.0),
 }
 
 

@@ -31,7 +31,10 @@ the starting site:
   * ``u85kev_uo2_300k_recoil`` -- 5120 U-235 recoils of 85 keV (the recoil
     of a Pu-239 alpha decay), 200 bins of 5 A;
   * ``kr85mev_uo2_300k_recoil`` -- 1024 Kr fission fragments of 85 MeV,
-    400 bins of 250 A (ranges of several micrometres).
+    400 bins of 400 A (ranges of several micrometres), with the energy term
+    of the time step at 100 eV: 0.05 A steps cannot resolve the closest
+    approaches of an 85 MeV ion (~1e-3 A), and without the term a track can
+    gain several times its energy.
 The thermal displacement of the UO2 lattice comes from MD data the paper
 cites but does not give; these workloads use the 0.076 A of the others.
 """
@@ -131,7 +134,7 @@ WORKLOADS = {
     "kr85mev_uo2_300k_recoil": dict(
         _BASE, ion=KR, energy=85.0e6, n_ions=1024, lattice="fluorite", a=5.4704, n=3,
         sigma=0.076, species=[U, O16], target="bulk", beam_mode="recoil", step_cap=10_000_000,
-        thresholds=_geom(2000.0, 60000.0, 8), n_bins=400, bin_w=250.0),
+        de_max=100.0, thresholds=_geom(20000.0, 100000.0, 8), n_bins=400, bin_w=400.0),
 }
 
 

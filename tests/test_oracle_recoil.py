@@ -15,7 +15,11 @@ ions starting on a lattice site in a random direction, Sec. 4.1, 4.2).
   are symmetric about the start (mean position 0 within its error);
 * energy balance of a recoil track with the damage map centred on the start,
   and the map receives deposits on both sides of z = 0;
-* adaptive cloning on the distance: weights sum to the primaries exactly.
+* adaptive cloning on the distance: weights sum to the primaries exactly;
+* 85 MeV Kr: with the energy term of the time step the energy balance of a
+  track holds (0.5 %) and its range stays below the drag-only bound; without
+  it, unresolved close collisions create energy (the same track gains
+  several times E0 and overshoots the bound).
 """
 import numpy as np
 import pytest
@@ -180,3 +184,26 @@ def test_adaptive_cloning_on_the_distance(O):
     th = r["thresholds"]
     assert th.shape[1] == 8 and np.all(np.diff(th, axis=1) > 0)
     assert r["clones"] > 0
+
+
+def test_energy_term_keeps_85_mev_tracks_conservative(O):
+    from concurrent.futures import ThreadPoolExecutor
+    base = dict(thresholds=[], damage_n=64, damage_voxel=5000.0)
+    wk = workload("kr85mev_uo2_300k_recoil", **base)
+    w0 = workload("kr85mev_uo2_300k_recoil", de_max=0.0, **base)
+    assert wk["de_max"] > 0
+
+    def balance(w):
+        e = O.track_energy(O.params(w), 0, 0)
+        rest = e["ke_ion"] + e["pe"] + e["e_elec"] + e["deposited"] + e["below_threshold"] + e["ke_window"]
+        return rest / e["E0"] - 1.0
+
+    def rng(w):
+        return O.run(O.params(w), 1, seed=0, threads=1)["records"]["z"][0]
+
+    with ThreadPoolExecutor(4) as ex:     # the oracle releases the GIL
+        b1, b0, z1, z0 = ex.map(lambda f: f[0](f[1]), [(balance, wk), (balance, w0), (rng, wk), (rng, w0)])
+    M, E = KR["M"], wk["energy"]
+    bound = M * (np.sqrt(2 * E / M) - np.sqrt(2 * wk["e_stop"] / M)) / O.gamma_ls(O.params(wk))
+    assert abs(b1) < 5e-3 and z1 < bound
+    assert b0 > 0.5 and z0 > bound

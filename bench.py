@@ -43,11 +43,17 @@ TRAFFIC_PER_LAUNCH = 414_210
 
 
 def _ion_name(w):
-    return {5.0: "B-11", 33.0: "As-75", 18.0: "Ar-40"}.get(w["ion"]["Z"], "Z=%g" % w["ion"]["Z"])
+    return {5.0: "B-11", 33.0: "As-75", 18.0: "Ar-40", 92.0: "U-235", 36.0: "Kr"}.get(w["ion"]["Z"],
+                                                                                    "Z=%g" % w["ion"]["Z"])
 
 
 def _target_name(w):
-    base = "Si(100)" if w["lattice"] == "diamond" else "CeO2 fluorite"
+    if w["lattice"] == "diamond":
+        base = "Si(100)"
+    else:
+        base = "%s fluorite" % ("UO2" if w["species"][0]["Z"] == 92.0 else "CeO2")
+    if w.get("target") == "bulk":
+        base += " (bulk, on-lattice recoils)"
     temp = "300 K sigma %.3f A" % w["sigma"] if w["sigma"] > 0 else "0 K"
     model = {"none": "ZBL ion-target only", "tersoff": "Tersoff+ZBL", "buckingham": "Buckingham+ZBL"}[w["tt"]]
     return "%s %s, %s" % (base, temp, model)

@@ -66,6 +66,12 @@ extern "C" {
 
 #define REED_BEAM_FIXED 0  /* fixed tilt, rotation uniform in [rot_lo, rot_hi) */
 #define REED_BEAM_CONE 1   /* direction uniform in solid angle within tilt of [001] */
+#define REED_BEAM_RECOIL 2 /* bulk targets only: start on the lattice site at the
+                              origin, direction uniform over the sphere (Sec. 4.1) */
+
+#define REED_TARGET_SURFACE 0 /* target occupies z >= 0 with a (001) surface */
+#define REED_TARGET_BULK 1    /* infinite crystal; the site of basis atom 0 of cell
+                                 (0,0,0) is vacant (the recoil atom's own site) */
 
 #define REED_TRACK_STOPPED 1        /* E < e_stop: tallied at its depth */
 #define REED_TRACK_BACKSCATTERED 2  /* left through the surface (z < -rc, vz < 0) */
@@ -74,16 +80,18 @@ extern "C" {
 
 /* ---- configuration structs (plain data, copied by the library) -------- */
 
-/* Target lattice and window (Sec. 2 "Second"; Fig. "moving cell").  The
- * target occupies z >= 0 with a (001) surface.  The window holds window_n^3
- * cells around the ion's cell (odd n) or its nearest cell corner (even n).
- * With target-target forces, frozen_margin outer cell layers are kept fixed
- * (they provide the environment of the integrated inner cells). */
+/* Target lattice and window (Sec. 2 "Second"; Fig. "moving cell").  A
+ * SURFACE target occupies z >= 0 with a (001) surface; a BULK target fills
+ * space and is run with REED_BEAM_RECOIL, the on-lattice recoils of the
+ * paper's UO2 runs (Sec. 4.1, 4.2).  The window holds window_n^3 cells around
+ * the ion's cell (odd n) or its nearest cell corner (even n).  With
+ * target-target forces, frozen_margin outer cell layers are kept fixed (they
+ * provide the environment of the integrated inner cells). */
 typedef struct {
     int32_t kind;          /* REED_LATTICE_* */
     int32_t window_n;      /* cells per window edge, 2..6 */
     int32_t frozen_margin; /* 0 or 1 */
-    int32_t reserved;
+    int32_t target;        /* REED_TARGET_* */
     double a;              /* lattice constant, A (> 2 rc / (window_n - 1) advised) */
     double sigma;          /* thermal displacement RMS per Cartesian coordinate, A (Sec. 4.1) */
 } reed_lattice;
@@ -98,7 +106,7 @@ typedef struct {
  * "First") times exp(sum_i spline_c[i] B_i(ln r)) (cubic B-splines centred on
  * ln r = ln{0.2,0.35,0.6,1.0,1.7,3.0} A; all zero = pure ZBL), tapered to
  * zero between r_taper and rc with a C2 quintic.  Electronic stopping (Sec. 2
- * "Third"): drag F = -gamma (1 + s_loc (rho/rho0 - 1)) v inside z >= 0,
+ * "Third"): drag F = -gamma (1 + s_loc (rho/rho0 - 1)) v inside the target,
  * gamma = s_e * Lindhard-Scharff, rho = sum over atoms of S(r) exp(-r/lam_loc). */
 typedef struct {
     double rc, r_taper;          /* A */
@@ -196,7 +204,7 @@ typedef struct {
 typedef struct {
     uint64_t id;        /* track id (primaries: first_id + i; clones: hashed) */
     uint64_t primary;   /* id of the primary whose lineage it belongs to */
-    double z;           /* depth at the end of the track, A */
+    double z;           /* depth at the end of the track, A (BULK: distance from the start) */
     double t;           /* simulated time, tau (1 tau = 10.1805 fs) */
     int64_t steps;      /* integration steps of the track's history (a clone counts its
                            parent's steps before the split; step_cap applies to this) */
@@ -239,7 +247,10 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
 /* Run n_ions primary tracks (ids opt->first_id ...) of an ion (Z, M amu) at
  * energy_eV launched at z = -rc with lateral position uniform in the (0,0)
  * surface cell and direction from tilt_deg and rotation U[rot_deg_lo,
- * rot_deg_hi) (or a cone of half-angle tilt_deg), Sec. 2.  Every primary is
+ * rot_deg_hi) (or a cone of half-angle tilt_deg), Sec. 2 -- or, on a BULK
+ * target with REED_BEAM_RECOIL, from the lattice site at the origin in a
+ * direction uniform over the sphere (the angles are then ignored), its depth
+ * being the distance from that site.  Every primary is
  * followed, with all its clones, until it stops, leaves through the surface
  * or reaches step_cap; results accumulate into the context's tallies until
  * reed_reset.  seed selects the random streams (Philox4x32-10 keyed by seed
@@ -251,7 +262,8 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
  * is out of work, donated to a shared pool that idle CTAs take from (the
  * paper's host handing returned clones to free clients, Sec. 3).
  * Returns REED_OK, REED_W_NEIGHBOR (completed; see nb_overflow), or an error:
- * REED_E_ARG, REED_E_SMEM, REED_E_CUDA, REED_E_NOMEM; REED_E_QUEUE_FULL and
+ * REED_E_ARG (also a RECOIL beam on a SURFACE target or the reverse, or the
+ * adjoint on a BULK target), REED_E_SMEM, REED_E_CUDA, REED_E_NOMEM; REED_E_QUEUE_FULL and
  * REED_E_NONFINITE mean the run completed but clones or tracks were lost
  * (counted in reed_stats); REED_E_TIMEOUT means a CTA out of work stopped
  * polling the clone pool after opt->pool_poll_limit polls (donated clones may
@@ -262,7 +274,8 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
 
 /* Weighted range profile (Sec. 2): bins_out[n_bins] (host or device, FP64)
  * receives sum of weights 2^-level of stopped tracks per depth bin
- * [b*w, (b+1)*w); extra3 (host or device, may be NULL) receives
+ * [b*w, (b+1)*w) (depth = z, or on a BULK target the distance from the
+ * start; cloning depths use the same coordinate); extra3 (host or device, may be NULL) receives
  * {stopped above the surface, stopped beyond the last bin, backscattered}.
  * n_bins must equal the tally's bin count.  Errors: REED_E_STATE (no run),
  * REED_E_ARG. */
@@ -301,8 +314,10 @@ int reed_grad(reed_ctx* ctx, double sigma, int n_bins, double bin_width, const d
 int reed_set_theta(reed_ctx* ctx, const double* theta8);
 
 /* Cumulative damage map of all runs since init/reset: out (host or device)
- * receives n^3 doubles (eV, index (ix n + iy) n + iz), overflow (may be
- * NULL) the energy deposited outside the grid.  n must equal damage_n. */
+ * receives n^3 doubles (eV, index (ix n + iy) n + iz; voxel (0,0,0) starts
+ * at (-n v / 2, -n v / 2, 0), on a BULK target at (-n v / 2) in all three),
+ * overflow (may be NULL) the energy deposited outside the grid.  n must
+ * equal damage_n. */
 int reed_damage_map(reed_ctx* ctx, double* out, int n, double* overflow);
 
 /* Counters of all runs since init/reset (host pointer). */
@@ -377,7 +392,7 @@ int reed_set_damage_feedback(reed_ctx* ctx, double dose_scale, double e_crit, do
 
 /* Replace the context's cumulative damage map: map (host or device) holds
  * n^3 voxels of voxel A ([ix][iy][iz], x and y centred on the entry cell, z
- * from the surface) and the overflow, as reed_damage_map returns it, e.g. the
+ * from the surface; on a BULK target all three centred on the start) and the overflow, as reed_damage_map returns it, e.g. the
  * sum of several processes' maps.  Later runs must use the same n and voxel.
  * REED_E_ARG for n outside 1..512 or voxel <= 0. */
 int reed_set_damage_map(reed_ctx* ctx, const double* map, int n, double voxel);
@@ -417,7 +432,8 @@ int reed_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t
 /* Atoms of absolute cell (ix,iy,iz) as the stepper creates them for a track
  * with Philox key `key` (Sec. 2, Sec. 4.1): xyz_out (host, 3*12 doubles,
  * absolute coordinates), species_out (host, 12 int32).  Returns the atom count
- * (0 above the surface) or a negative status. */
+ * (0 above the surface; on a BULK target cell (0,0,0) lacks basis atom 0) or
+ * a negative status. */
 int reed_cell_atoms(reed_ctx* ctx, uint64_t key, int32_t ix, int32_t iy, int32_t iz,
                     double* xyz_out, int32_t* species_out);
 

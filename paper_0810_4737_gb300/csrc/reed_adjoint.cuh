@@ -227,7 +227,7 @@ __device__ void replay_step(const DevParams& P, const HotParams<R>& H, Win<R, TT
         const R h = R(0.5) * dt * H.invM1;
         for (int d = 0; d < 3; ++d) {
             const R fe = -kd * I.v[d];
-            I.v[d] += h * (I.f[d] + fe);
+            add_velocity<R>(I, d, h * (I.f[d] + fe));
         }
         for (int d = 0; d < 3; ++d) {
             const R dx = dt * I.v[d];
@@ -276,7 +276,7 @@ __device__ void replay_step(const DevParams& P, const HotParams<R>& H, Win<R, TT
         const R h = R(0.5) * sr.dt * H.invM1;
         for (int d = 0; d < 3; ++d) {
             const R fe = -kd * I.v[d];
-            I.v[d] += h * (I.f[d] + fe);
+            add_velocity<R>(I, d, h * (I.f[d] + fe));
         }
         I.t += (double)sr.dt;
         I.steps += 1;

@@ -288,6 +288,7 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.kind = L.kind;
     P.n = L.window_n;
     P.margin = L.frozen_margin;
+    P.bulk = L.target == REED_TARGET_BULK;
     P.nb = basis_count(L.kind);
     P.na = P.n * P.n * P.n * P.nb;
     P.nspec = ctx->nspec;
@@ -348,6 +349,7 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.dn = o.damage_n;
     P.dvox = o.damage_voxel > 0 ? o.damage_voxel : 10.0;
     P.dhalf = 0.5 * P.dn * P.dvox;
+    P.dzhalf = P.bulk ? P.dhalf : 0.0;
     P.dmin = o.damage_min;
     P.de_max = o.de_max > 0.0 ? o.de_max : 0.0;
     P.pool_polls = o.pool_poll_limit > 0 ? o.pool_poll_limit : (1ll << 26);
@@ -376,10 +378,24 @@ void set_feedback(const reed_ctx* ctx, DevParams& P, const double* map)
     P.fb_n = ctx->dn;
     P.fb_vox = ctx->dvox;
     P.fb_half = 0.5 * ctx->dn * ctx->dvox;
+    P.fb_zhalf = ctx->lat.target == REED_TARGET_BULK ? P.fb_half : 0.0;
     P.fb_dose = ctx->fb_dose;
     P.fb_atoms = basis_count(ctx->lat.kind) * std::pow(ctx->dvox / ctx->lat.a, 3.0);
     P.fb_ec = ctx->fb_ec;
     P.sigma_am = ctx->fb_sam;
+}
+
+// Beam and target geometry must agree: recoils start inside a bulk target,
+// the other beams enter through the surface.  The adjoint's loss is on the
+// depth below a surface.
+const char* beam_error(const reed_lattice& L, const reed_run_opts& o)
+{
+    if (o.beam_mode != REED_BEAM_FIXED && o.beam_mode != REED_BEAM_CONE && o.beam_mode != REED_BEAM_RECOIL)
+        return "beam_mode";
+    if ((o.beam_mode == REED_BEAM_RECOIL) != (L.target == REED_TARGET_BULK))
+        return "REED_BEAM_RECOIL goes with a BULK target and the other beams with a SURFACE target";
+    if (o.adjoint && L.target == REED_TARGET_BULK) return "the adjoint needs a SURFACE target";
+    return nullptr;
 }
 
 reed_run_opts default_opts()
@@ -541,6 +557,8 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
     if (lat->window_n < 2 || lat->window_n > 6) return fail(nullptr, REED_E_ARG, "window_n must be 2..6");
     if (lat->frozen_margin < 0 || 2 * lat->frozen_margin >= lat->window_n)
         return fail(nullptr, REED_E_ARG, "frozen_margin must be 0 or 1 and leave an integrated core");
+    if (lat->target != REED_TARGET_SURFACE && lat->target != REED_TARGET_BULK)
+        return fail(nullptr, REED_E_ARG, "unknown target geometry %d", lat->target);
     if (!(lat->a > 0.5) || !(lat->sigma >= 0.0)) return fail(nullptr, REED_E_ARG, "invalid lattice constant or sigma");
     int need = lat->kind == REED_LATTICE_FLUORITE ? 2 : 1;
     if (n_species != need) return fail(nullptr, REED_E_ARG, "lattice needs %d species, got %d", need, n_species);
@@ -616,7 +634,7 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     for (int i = 1; i < o.n_thresholds; ++i)
         if (!(o.thresholds[i] > o.thresholds[i - 1])) return fail(ctx, REED_E_ARG, "thresholds must ascend");
     if (o.n_bins < 1 || !(o.bin_width > 0)) return fail(ctx, REED_E_ARG, "invalid histogram");
-    if (o.beam_mode != REED_BEAM_FIXED && o.beam_mode != REED_BEAM_CONE) return fail(ctx, REED_E_ARG, "beam_mode");
+    if (const char* m = beam_error(ctx->lat, o)) return fail(ctx, REED_E_ARG, "%s", m);
     if (o.precision != REED_PREC_MIXED && o.precision != REED_PREC_FP64) return fail(ctx, REED_E_ARG, "precision");
     if (o.threads_per_track && !valid_threads(o.threads_per_track))
         return fail(ctx, REED_E_ARG, "threads_per_track must be 0, 32, 64, 128 or 256");
@@ -1439,6 +1457,8 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     if (lat->window_n < 2 || lat->window_n > 6) return fail(nullptr, REED_E_ARG, "window_n must be 2..6");
     if (lat->frozen_margin < 0 || 2 * lat->frozen_margin >= lat->window_n)
         return fail(nullptr, REED_E_ARG, "frozen_margin must be 0 or 1 and leave an integrated core");
+    if (lat->target != REED_TARGET_SURFACE && lat->target != REED_TARGET_BULK)
+        return fail(nullptr, REED_E_ARG, "unknown target geometry %d", lat->target);
     if (!(lat->a > 0.5) || !(lat->sigma >= 0.0)) return fail(nullptr, REED_E_ARG, "invalid lattice constant or sigma");
     if (n_species != (lat->kind == REED_LATTICE_FLUORITE ? 2 : 1))
         return fail(nullptr, REED_E_ARG, "wrong number of species");
@@ -1461,7 +1481,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     for (int i = 1; i < o.n_thresholds; ++i)
         if (!(o.thresholds[i] > o.thresholds[i - 1])) return fail(nullptr, REED_E_ARG, "thresholds must ascend");
     if (o.n_bins < 1 || !(o.bin_width > 0)) return fail(nullptr, REED_E_ARG, "invalid histogram");
-    if (o.beam_mode != REED_BEAM_FIXED && o.beam_mode != REED_BEAM_CONE) return fail(nullptr, REED_E_ARG, "beam_mode");
+    if (const char* m = beam_error(*lat, o)) return fail(nullptr, REED_E_ARG, "%s", m);
     if (o.precision != REED_PREC_MIXED && o.precision != REED_PREC_FP64) return fail(nullptr, REED_E_ARG, "precision");
     if (o.threads_per_track && !valid_threads(o.threads_per_track))
         return fail(nullptr, REED_E_ARG, "threads_per_track must be 0, 32, 64, 128 or 256");

@@ -66,11 +66,12 @@ struct DevParams {
     HotParams<double> hd;
     // lattice and window (Sec. 2 "Second")
     int kind, n, margin, nb, na, nspec, half_n;   // half_n = n / 2
+    int bulk;                                      // 1: infinite crystal, vacancy at the origin site
     int g_nb, g_nbins;                             // neighbour-search grid: bins per axis, in all
     // damage feedback: the cumulative map new cells read (null = off)
     const double* fb_map;
     int fb_n;
-    double fb_vox, fb_half, fb_dose, fb_atoms, fb_ec, sigma_am;
+    double fb_vox, fb_half, fb_zhalf, fb_dose, fb_atoms, fb_ec, sigma_am;
     double a, inv_a, sigma, anchor_shift;          // anchor_shift = 0.5 for even n
     double bas[REED_MAX_BASIS][3];
     int bspec[REED_MAX_BASIS];
@@ -104,9 +105,10 @@ struct DevParams {
     int nthr;
     double thr[REED_MAX_THR];
     int thr_from_device;               // read the depths from DevBuf::thr (adaptive epochs)
-    // cumulative damage map: dn^3 voxels of dvox, origin (-dhalf, -dhalf, 0)
+    // cumulative damage map: dn^3 voxels of dvox, origin (-dhalf, -dhalf, -dzhalf)
+    // with dzhalf = 0 (surface target) or dhalf (bulk target)
     int dn;
-    double dvox, dhalf, dmin;
+    double dvox, dhalf, dzhalf, dmin;
     // truncated-segment adjoint: segment length, checkpoint spacing, ring size
     int adjoint, adj_seg, adj_every, adj_nck;
     long long stop_after;              // stop handing out primaries after this many tracks (0: never)

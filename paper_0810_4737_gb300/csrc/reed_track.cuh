@@ -39,10 +39,11 @@ enum { EV_NONE = 0, EV_END = 1, EV_CLONE = 2, EV_CKPT = 3 };
 // time and the energy given to electronic stopping are FP64 accumulators;
 // velocity, force and the step arithmetic are in the force-pass type R, so
 // the mixed form executes only a handful of FP64 additions per step.
-template <typename R> struct IonState {
+template <typename R> struct alignas(16) IonState {
     double x[3];          // absolute position, A
     double t, e_elec;     // time (tau), energy removed by the drag (eV)
     R v[3], f[3];         // velocity (A/tau), conservative force (eV/A)
+    R vlo[3];             // FP32 form: the rounding error carried with v (v + vlo, see add_velocity)
     R rho, vmax2;         // local density at x; fastest atom's speed^2
     R pmax;               // largest |F . v| over the integrated atoms (energy term of dt)
     long long steps;
@@ -203,7 +204,9 @@ __device__ __forceinline__ void slot_coords(const DevParams& P, int i, int s[3],
 
 // Create the atom of slot i for a window anchored at A (Sec. 2: new cells
 // are a perfect lattice plus a statistical realisation; Sec. 4.1: Gaussian
-// thermal displacements).  Cells with z index < 0 are above the surface.
+// thermal displacements).  Cells with z index < 0 are above the surface of a
+// surface target; a bulk target fills space and lacks the atom of the site
+// the recoil starts from (basis atom 0 of cell (0,0,0)).
 template <typename R>
 __device__ void make_atom(const DevParams& P, uint64_t key, int i, const int A[3], V4<R>& p, V4<R>& v)
 {
@@ -218,7 +221,7 @@ __device__ void make_atom(const DevParams& P, uint64_t key, int i, const int A[3
         if (o < P.margin || o > P.n - 1 - P.margin) active = 0;
     }
     v.x = v.y = v.z = v.w = R(0);
-    if (c[2] < 0) {
+    if (P.bulk ? (b == 0 && c[0] == 0 && c[1] == 0 && c[2] == 0) : c[2] < 0) {
         p.x = p.y = p.z = R(0);
         p.w = R(REED_W_EMPTY);
         return;
@@ -229,7 +232,8 @@ __device__ void make_atom(const DevParams& P, uint64_t key, int i, const int A[3
     // the cell's centre and N lattice atoms per voxel
     double sig = P.sigma;
     if (P.fb_map) {
-        const double cc[3] = {(c[0] + 0.5) * P.a + P.fb_half, (c[1] + 0.5) * P.a + P.fb_half, (c[2] + 0.5) * P.a};
+        const double cc[3] = {(c[0] + 0.5) * P.a + P.fb_half, (c[1] + 0.5) * P.a + P.fb_half,
+                              (c[2] + 0.5) * P.a + P.fb_zhalf};
         int vv[3];
         bool in = true;
 #pragma unroll
@@ -317,7 +321,7 @@ __device__ __forceinline__ void deposit_damage(const DevParams& P, const DevBuf&
     const double x = (double)p.x + (double)A[0] * P.a, y = (double)p.y + (double)A[1] * P.a,
                  z = (double)p.z + (double)A[2] * P.a;
     const int ix = (int)floor((x + P.dhalf) / P.dvox), iy = (int)floor((y + P.dhalf) / P.dvox),
-              iz = (int)floor(z / P.dvox);
+              iz = (int)floor((z + P.dzhalf) / P.dvox);
     const size_t n = (size_t)P.dn;
     size_t cell = n * n * n;   // overflow
     if (ix >= 0 && iy >= 0 && iz >= 0 && ix < P.dn && iy < P.dn && iz < P.dn) cell = ((size_t)ix * n + iy) * n + iz;
@@ -881,6 +885,14 @@ __device__ __forceinline__ void gather_partials(Win<R, TT>& W, R out[REED_NRED])
     for (int c = 0; c < REED_NRED; ++c) out[c] = acc[c];
 }
 
+// Depth of the ion for the tallies and the cloning depths: z below a
+// surface, or the distance from the starting site in a bulk target.
+template <typename R> __device__ __forceinline__ double track_depth(const DevParams& P, const IonState<R>& I)
+{
+    if (!P.bulk) return I.x[2];
+    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(I.x[0], I.x[0]), __dmul_rn(I.x[1], I.x[1])), __dmul_rn(I.x[2], I.x[2])));
+}
+
 // Depth bin tally and per-track record of a finished track (Sec. 3: result
 // messages become atomics on device tallies).
 template <typename R>
@@ -890,8 +902,8 @@ __device__ long long finish_track(const DevParams& P, const DevBuf& B, const Ion
     const double w = ldexp(1.0, -I.level);
     if (status >= REED_TRACK_STOPPED && status <= REED_TRACK_TRUNCATED)
         atomicAdd(&B.counters[C_STOP + status - REED_TRACK_STOPPED], 1ull);
+    const double z = track_depth(P, I);
     if (status == REED_TRACK_STOPPED) {
-        const double z = I.x[2];
         int bin;
         if (z < 0.0) bin = P.nbins;
         else {
@@ -915,7 +927,7 @@ __device__ long long finish_track(const DevParams& P, const DevBuf& B, const Ion
             reed_track_record r;
             r.id = I.id;
             r.primary = I.primary;
-            r.z = I.x[2];
+            r.z = z;
             r.t = I.t;
             r.steps = I.steps;
             r.level = I.level;
@@ -927,8 +939,25 @@ __device__ long long finish_track(const DevParams& P, const DevBuf& B, const Ion
     return kept;
 }
 
+// Add a half kick to the ion's velocity.  In FP32 the sum is kept as two
+// floats, v + vlo (Knuth's TwoSum), so that increments of a few ulp -- the drag
+// on an MeV ion over its 0.05 A steps -- do not round systematically: a plain
+// FP32 sum shortened the 85 MeV Kr drag range by 0.7 %, the pair by < 1e-6.
+template <typename R> __device__ __forceinline__ void add_velocity(IonState<R>& I, int d, R inc)
+{
+    if constexpr (sizeof(R) == 4) {
+        const float a = I.v[d], b = __fadd_rn(inc, I.vlo[d]);
+        const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+        I.vlo[d] = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+        I.v[d] = s;
+    } else {
+        I.v[d] += inc;
+    }
+}
+
 // Launch a primary (Sec. 2; lateral position uniform in the (0,0) surface
-// cell, start at z = -rc).
+// cell, start at z = -rc; or a recoil from the origin site of a bulk target,
+// the on-lattice ions of Sec. 4.1).
 template <typename R> __device__ void launch_primary(const DevParams& P, IonState<R>& I, long long pidx)
 {
     I.id = (unsigned long long)(P.first_id + pidx);
@@ -941,17 +970,28 @@ template <typename R> __device__ void launch_primary(const DevParams& P, IonStat
         const double ct = 1.0 - unit_open(w[2]) * (1.0 - P.cos_tmax);
         th = acos(ct);
         ph = 2.0 * REED_PI * unit_open(w[3]);
+    } else if (P.beam_mode == REED_BEAM_RECOIL) {
+        // uniform over the sphere: cos(theta) uniform in (-1, 1)
+        th = acos(1.0 - 2.0 * unit_open(w[2]));
+        ph = 2.0 * REED_PI * unit_open(w[3]);
     } else {
         th = P.tilt;
         ph = P.rot_lo + P.rot_span * unit_open(w[2]);
     }
-    I.x[0] = P.a * unit_open(w[0]);
-    I.x[1] = P.a * unit_open(w[1]);
-    I.x[2] = -P.rc;
+    if (P.beam_mode == REED_BEAM_RECOIL) {   // on the site of basis atom 0 of cell (0,0,0)
+        I.x[0] = P.bas[0][0] * P.a;
+        I.x[1] = P.bas[0][1] * P.a;
+        I.x[2] = P.bas[0][2] * P.a;
+    } else {
+        I.x[0] = P.a * unit_open(w[0]);
+        I.x[1] = P.a * unit_open(w[1]);
+        I.x[2] = -P.rc;
+    }
     const double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
     I.v[0] = R(P.v0 * st * cp);
     I.v[1] = R(P.v0 * st * sp);
     I.v[2] = R(P.v0 * ct);
+    I.vlo[0] = I.vlo[1] = I.vlo[2] = R(0);
     I.f[0] = I.f[1] = I.f[2] = R(0);
     I.rho = R(0);
     I.vmax2 = R(0);
@@ -971,6 +1011,12 @@ template <typename R> __device__ void set_frame(const DevParams& P, TrackShared<
     const IonState<R>& I = S->ion;
     for (int d = 0; d < 3; ++d) S->rel[d] = R(I.x[d] - (double)I.A[d] * P.a);
     const double z0 = (double)I.A[2] * P.a;
+    if (P.bulk) {   // no surface; the depth checks run on the distance from the start
+        S->zthr = I.level < S->nthr ? R(-1e30) : R(1e30);
+        S->zback = R(-1e30);
+        S->zsurf = R(-1e30);
+        return;
+    }
     S->zthr = I.level < S->nthr ? R(S->thr[I.level] - z0) : R(1e30);
     S->zback = R(-P.rc - z0);
     S->zsurf = R(-z0);
@@ -1005,7 +1051,7 @@ template <typename R> __device__ void ion_prologue(const DevParams& P, const Hot
     for (int d = 0; d < 3; ++d) {
         const R fe = -kd * I.v[d];
         de -= fe * I.v[d];
-        I.v[d] += h * (I.f[d] + fe);
+        add_velocity<R>(I, d, h * (I.f[d] + fe));
     }
     I.e_elec += (double)(R(0.5) * dt * de);
     int moved = 0;
@@ -1045,7 +1091,7 @@ __device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShar
     for (int d = 0; d < 3; ++d) {
         const R fe = -kd * I.v[d];
         de -= fe * I.v[d];
-        I.v[d] += h * (I.f[d] + fe);
+        add_velocity<R>(I, d, h * (I.f[d] + fe));
     }
     I.e_elec += (double)(R(0.5) * dt * de);
     I.t += (double)dt;
@@ -1061,7 +1107,8 @@ __device__ int ion_epilogue(const DevParams& P, const HotParams<R>& H, TrackShar
     int nc = 0;
     if (S->rel[2] >= S->zthr) {
         // passed one (or more) cloning depths: count them on the FP64 depth
-        while (I.level + nc < S->nthr && I.x[2] >= S->thr[I.level + nc]) ++nc;
+        const double z = track_depth(P, I);
+        while (I.level + nc < S->nthr && z >= S->thr[I.level + nc]) ++nc;
     }
     S->nclone = nc;
     return nc ? EV_CLONE : EV_NONE;

@@ -20,14 +20,15 @@ W_NEIGHBOR = 1   # completed; some neighbour lists were truncated (stats["nb_ove
 LATTICE = {"diamond": 0, "fluorite": 1}
 TT = {"none": 0, "tersoff": 1, "buckingham": 2}
 PREC_MIXED, PREC_FP64 = 0, 1
-BEAM = {"fixed": 0, "cone": 1}
+BEAM = {"fixed": 0, "cone": 1, "recoil": 2}
+TARGET = {"surface": 0, "bulk": 1}
 STOPPED, BACKSCATTERED, TRUNCATED, FAILED = 1, 2, 3, 4
 TAU_FS = 10.180505710
 
 
 class reed_lattice(C.Structure):
     _fields_ = [("kind", C.c_int32), ("window_n", C.c_int32), ("frozen_margin", C.c_int32),
-                ("reserved", C.c_int32), ("a", C.c_double), ("sigma", C.c_double)]
+                ("target", C.c_int32), ("a", C.c_double), ("sigma", C.c_double)]
 
 
 class reed_species(C.Structure):
@@ -170,7 +171,7 @@ def _check(rc, ctx=None):
 
 def lattice_struct(w) -> reed_lattice:
     return reed_lattice(kind=LATTICE[w["lattice"]], window_n=int(w["n"]), frozen_margin=int(w["margin"]),
-                        reserved=0, a=float(w["a"]), sigma=float(w["sigma"]))
+                        target=TARGET[w.get("target", "surface")], a=float(w["a"]), sigma=float(w["sigma"]))
 
 
 def species_array(w):

@@ -64,7 +64,8 @@ def run_adaptive(engine, n_ions: int, epoch_size: int, n_initial: int, initial_d
                  world: int = 1, allreduce=None) -> list:
     """Run the adaptive schedule on this rank; returns the depths used by each
     enhanced epoch.  allreduce(profile) must return the element-wise sum over
-    ranks (it is called by every rank at the same points)."""
+    ranks (it is called by every rank at the same points, also when world is
+    1 if it is given)."""
     if world > 1 and allreduce is None:
         raise ValueError("several ranks need an allreduce")
     engine.set_depths(np.asarray(initial_depths, dtype=np.float64))
@@ -73,7 +74,7 @@ def run_adaptive(engine, n_ions: int, epoch_size: int, n_initial: int, initial_d
         if ep.enhanced:
             if ep.update:
                 prof = engine.local_profile()
-                engine.update_depths(allreduce(prof) if world > 1 else prof)
+                engine.update_depths(allreduce(prof) if allreduce is not None else prof)
             history.append(np.array(engine.depths(), dtype=np.float64))
         first, count = rank_block(ep.first, ep.count, rank, world)
         engine.run(first, count, ep.enhanced)

@@ -108,3 +108,44 @@ def test_sharded_driver_matches_adaptive_run(R):
     assert np.array_equal(np.array(hist), ref_th[:, :6])
     assert np.array_equal(bins, ref_bins) and np.array_equal(extra, ref_extra)
     assert st["tracks"] == ref_st["tracks"] and st["steps"] == ref_st["steps"]
+
+
+def test_sharded_driver_over_nccl(R):
+    """The multi-process driver with its histogram sum done by a NCCL
+    all_reduce on the device (one rank on this GPU): the same depths and
+    profile as the in-graph adaptive run."""
+    import os
+    import socket
+    import torch
+    import torch.distributed as dist
+    from paper_0810_4737_gb300 import sharded
+    os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    w = workload("b1kev_si_0k_zbl", **W)
+    n, epoch, ninit = 1250, 400, 50
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n, seed=9, adaptive=True, n_initial=ninit, epoch_size=epoch)
+        ref_bins, ref_extra = ctx.profile()
+        ref_th = ctx.thresholds()
+    torch.cuda.set_device(0)
+    dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, world_size=1, rank=0)
+    calls = []
+
+    def allreduce(t):
+        assert t.is_cuda and t.dtype == torch.float64
+        dist.all_reduce(t)
+        calls.append(1)
+        return t
+    try:
+        with R.Reed(w) as ctx:
+            eng = sharded.ReedShard(ctx, seed=9)
+            hist = sharded.run_adaptive(eng, n, epoch, ninit, w["thresholds"], rank=0, world=1,
+                                        allreduce=allreduce)
+            bins, extra = ctx.profile()
+    finally:
+        dist.destroy_process_group()
+    assert len(calls) == len(hist) > 1
+    assert np.array_equal(np.array(hist), ref_th[:, :6])
+    assert np.array_equal(bins, ref_bins) and np.array_equal(extra, ref_extra)

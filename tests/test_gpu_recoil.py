@@ -1,0 +1,233 @@
+"""GPU parity of the bulk UO2 target and the recoil beam (the paper's own
+runs: 85 keV U recoils and 85 MeV Kr fission fragments starting on a lattice
+site in a random direction, Sec. 4.1, 4.2) against the oracle, through the
+C ABI.
+
+* cell creation in a bulk target: cells above z = 0 are populated and the
+  recoil's own site is vacant (species bit-exact, positions 1e-12 A FP64);
+* the window along a path from the starting site to above z = 0 and back:
+  anchors, cells (the vacancy re-created) and positions as the oracle
+  (bit-exact / 1e-12 / 4e-6 A);
+* the first 50 steps of U and Kr recoils within 1e-4 A (both precisions);
+* the mixed form keeps an 85 MeV ion's drag-only range (closed form) to 2e-4;
+* U range statistics (distance from the start): mean and straggle within
+  their errors, KS p > 0.01; histogram = records;
+* the full 85 keV U workload with eight adaptive cloning distances: exact
+  weight accounting and the unenhanced distribution;
+* Kr: ranges of several micrometres as in the oracle;
+* the damage map is centred on the start; mismatched beam and target, and
+  the adjoint on a bulk target, are refused.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_0810_4737_gb300.workloads import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_0810_4737_gb300 import build, reed
+    build.build()
+    return reed
+
+
+def _wks(a, wa, b, wb):
+    xs = np.concatenate([a, b])
+    order = np.argsort(xs, kind="mergesort")
+    ca = np.cumsum(np.concatenate([wa / wa.sum(), np.zeros(len(b))])[order])
+    cb = np.cumsum(np.concatenate([np.zeros(len(a)), wb / wb.sum()])[order])
+    D = np.max(np.abs(ca - cb))
+    na = wa.sum() ** 2 / np.sum(wa ** 2)
+    nb = wb.sum() ** 2 / np.sum(wb ** 2)
+    return D, stats.kstwo.sf(D, int(round(na * nb / (na + nb))))
+
+
+def _mean_sd_se(z):
+    return np.mean(z), np.std(z), np.std(z) / np.sqrt(len(z))
+
+
+def test_bulk_cells_match_oracle(R, O):
+    w = workload("u85kev_uo2_300k_recoil")
+    p = O.params(w)
+    with R.Reed(w) as ctx:
+        for key in range(40):
+            for c in [(0, 0, 0), (0, 0, -1), (-1, 2, -3), (1, 1, 1), (0, -1, 0)]:
+                xg, sg = ctx.cell_atoms(key, *c)
+                xo, so = O.cell_atoms(p, key, *c)
+                assert len(xg) == (11 if c == (0, 0, 0) else 12)
+                assert np.array_equal(sg, so)
+                np.testing.assert_allclose(xg, xo, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bulk_window_matches_oracle(R, O, prec):
+    w = workload("u85kev_uo2_300k_recoil")
+    p = O.params(w)
+    rng = np.random.default_rng(5)
+    steps = rng.normal(size=(2500, 3)) * 0.06
+    steps[:1250, 2] -= 0.015                  # from the vacant site upwards, above z = 0 ...
+    steps[1250:, 2] += 0.015                  # ... and back: the start cell is created again
+    path = np.cumsum(steps, axis=0)
+    with R.Reed(w) as ctx:
+        ag, cg, bg, xg = ctx.window_replay(31, path, precision=prec)
+    ao, co, bo, xo = O.window_replay(p, 31, path)
+    assert path[:, 2].min() < -15.0 and len(co) == 27 * 12 - 1
+    assert np.array_equal(ag, ao)
+    kg, ko = np.lexsort(np.c_[cg, bg].T), np.lexsort(np.c_[co, bo].T)
+    assert np.array_equal(cg[kg], co[ko]) and np.array_equal(bg[kg], bo[ko])
+    np.testing.assert_allclose(xg[kg], xo[ko], rtol=0, atol=1e-12 if prec == 1 else 4e-6)
+
+
+def _trace_check(R, O, w, n_tracks, n_steps, prec, tol, seed=0):
+    p = O.params(w)
+    with R.Reed(w) as ctx:
+        # the tracks are cut after the traced steps (an 85 MeV track runs 2e6 steps)
+        ctx.run(n_ions=n_tracks, seed=seed, precision=prec, trace_tracks=n_tracks, trace_steps=n_steps,
+                thresholds=[], step_cap=4 * n_steps)
+        traj, anc = ctx.trace(n_tracks, n_steps)
+    for t in range(n_tracks):
+        ref, ranc = O.trace(p, seed, t, n_steps)
+        k = ref.shape[0]
+        err = np.max(np.abs(traj[t, :k, :3] - ref[:, :3]))
+        assert err < tol, (t, err)
+        np.testing.assert_allclose(traj[t, :k, 3], ref[:, 3], rtol=1e-12 if prec == 1 else 2e-5)
+        assert np.array_equal(anc[t, :k], ranc)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["u85kev_uo2_300k_recoil", "kr85mev_uo2_300k_recoil"])
+def test_first_50_steps_of_recoils(R, O, name, prec):
+    _trace_check(R, O, workload(name), 24, 50, prec, 1e-4)
+
+
+def test_mixed_form_keeps_the_drag_range_at_85_mev(R, O):
+    """A Kr-mass ion whose nuclear forces are switched off in effect (Z = 1e-3,
+    the drag rescaled to Kr's): every range is the drag ODE's closed form
+    M (v0 - v_stop) / gamma within 2e-4 over 2e6 steps.  The FP32 velocity is
+    carried as two floats; a plain FP32 sum falls 0.7 % short here."""
+    w = workload("kr85mev_uo2_300k_recoil", thresholds=[], ion={"Z": 1e-3, "M": 83.798})
+    g1 = O.gamma_ls(O.params(w))
+    w["s_e"] = 1.1 / g1
+    gam = O.gamma_ls(O.params(w))
+    M = w["ion"]["M"]
+    expect = M * (np.sqrt(2 * w["energy"] / M) - np.sqrt(2 * w["e_stop"] / M)) / gam
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=32, seed=0)
+        rec = ctx.records()
+    assert np.all(rec["status"] == 1)
+    assert np.max(np.abs(rec["z"] / expect - 1)) < 2e-4, (rec["z"].min(), rec["z"].max(), expect)
+
+
+def test_u_recoil_ranges_match_oracle(R, O):
+    w = workload("u85kev_uo2_300k_recoil", thresholds=[])
+    n_o, n_g = 2048, 8192
+    ref = O.run(O.params(w), n_o, seed=0, threads=os.cpu_count() or 1)["records"]
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n_g, seed=0)
+        rec = ctx.records()
+        st = ctx.stats()
+        bins, extra = ctx.profile()
+    assert st["tracks"] == n_g and np.all(rec["status"] == 1) and np.all(ref["status"] == 1)
+    zo, zg = ref["z"], rec["z"]
+    mo, do, eo = _mean_sd_se(zo)
+    mg, dg, eg = _mean_sd_se(zg)
+    assert abs(mg - mo) < 4 * np.hypot(eo, eg), (mg, mo)
+    assert abs(dg / do - 1) < 4 * np.sqrt(0.5 / n_o) + 0.02, (dg, do)
+    D, pval = _wks(zo, np.ones(len(zo)), zg, np.ones(len(zg)))
+    assert pval > 0.01, (D, pval)
+    # the range coordinate: histogram of the records, nothing above a surface or backscattered
+    h = np.bincount(np.minimum((zg // w["bin_w"]).astype(int), w["n_bins"]), minlength=w["n_bins"] + 1)
+    np.testing.assert_array_equal(bins, h[:-1])
+    assert extra[0] == 0 and extra[1] == h[-1] and extra[2] == 0
+
+
+def test_u_recoil_workload_adaptive_full_size(R):
+    """5120 U recoils with eight cloning distances placed adaptively (50
+    unenhanced primaries, then epochs): exact weights, no lost clone, and the
+    weighted range distribution of the unenhanced run."""
+    w = workload("u85kev_uo2_300k_recoil")
+    n = int(w["n_ions"])
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n, seed=0, adaptive=True, n_initial=50, epoch_size=1024)
+        st = ctx.stats()
+        rec = ctx.records()
+        bins, extra = ctx.profile()
+        th = ctx.thresholds()
+    assert st["primaries"] == n and st["dropped_clones"] == 0 and st["failed"] == 0
+    assert st["tracks"] == n + st["clones"] == len(rec) and st["clones"] > n
+    wts = np.ldexp(1.0, -rec["level"].astype(int))
+    assert np.sum(wts) == n
+    assert bins.sum() + extra.sum() + st["w_trunc"] == n
+    assert np.all(np.diff(th[-1][:8]) > 0)
+    with R.Reed(dict(w, thresholds=[])) as ctx:
+        ctx.run(n_ions=n, seed=0)
+        plain = ctx.records()
+    D, pval = _wks(rec["z"], wts, plain["z"], np.ones(len(plain)))
+    assert pval > 0.01, (D, pval)
+
+
+def test_kr_fission_fragment_ranges_match_oracle(R, O):
+    w = workload("kr85mev_uo2_300k_recoil", thresholds=[])
+    n_o, n_g = 16, 128
+    ref = O.run(O.params(w), n_o, seed=0, threads=os.cpu_count() or 1)["records"]
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n_g, seed=0)
+        rec = ctx.records()
+        st = ctx.stats()
+    assert st["tracks"] == n_g and np.all(rec["status"] == 1) and np.all(ref["status"] == 1)
+    zo, zg = ref["z"], rec["z"]
+    assert 5e4 < np.mean(zg) < 1.5e5            # several micrometres
+    mo, _, eo = _mean_sd_se(zo)
+    mg, _, eg = _mean_sd_se(zg)
+    assert abs(mg - mo) < 4 * np.hypot(eo, eg), (mg, mo)
+    assert stats.ks_2samp(zo, zg).pvalue > 0.01
+
+
+def test_bulk_damage_map_is_centred(R, O):
+    w = workload("u85kev_uo2_300k_recoil", thresholds=[], damage_n=32, damage_voxel=20.0)
+    n = 256
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n, seed=2)
+        d, ov = ctx.damage_map()
+    r = O.run(O.params(w), n, seed=2, threads=os.cpu_count() or 1)
+    assert d[:, :, :16].sum() > 0 and d[:, :, 16:].sum() > 0
+    assert ov < 0.05 * d.sum()
+    # deposited energy per ion as in the oracle (same primaries, chaotic tracks: statistics)
+    assert abs(d.sum() / r["damage"].sum() - 1) < 0.1
+    iz = np.arange(32) + 0.5
+    prof_g, prof_o = d.sum(axis=(0, 1)), r["damage"].sum(axis=(0, 1))
+    cg, co = np.sum(iz * prof_g) / prof_g.sum(), np.sum(iz * prof_o) / prof_o.sum()
+    assert abs(cg - 16.0) < 1.0 and abs(co - 16.0) < 1.0     # centred on the start
+
+
+def test_beam_and_target_must_agree(R):
+    wb = workload("u85kev_uo2_300k_recoil")
+    with R.Reed(dict(wb, beam_mode="fixed")) as ctx:
+        with pytest.raises(R.ReedError) as e:
+            ctx.run(n_ions=4)
+        assert e.value.code == R.E_ARG
+        with pytest.raises(R.ReedError) as e:
+            ctx.run(n_ions=4, adjoint=True)
+        assert e.value.code == R.E_ARG
+    with R.Reed(wb) as ctx:
+        with pytest.raises(R.ReedError) as e:
+            ctx.run(n_ions=4, thresholds=[], adjoint=True)
+        assert e.value.code == R.E_ARG
+        ctx.run(n_ions=4, seed=1, thresholds=[])     # still usable
+        assert ctx.stats()["tracks"] == 4
+    ws = workload("b1kev_si_0k_zbl", beam_mode="recoil")
+    with R.Reed(ws) as ctx:
+        with pytest.raises(R.ReedError) as e:
+            ctx.run(n_ions=4)
+        assert e.value.code == R.E_ARG
+    # an unknown target code is refused by reed_init
+    lat = R.lattice_struct(wb)
+    lat.target = 7
+    with pytest.raises(R.ReedError) as e:
+        R.reed_init(lat, R.species_array(wb), 2, R.potentials_struct(wb))
+    assert e.value.code == R.E_ARG

@@ -96,6 +96,12 @@ def test_damage_map_matches_oracle(R, O):
     zg, zo = dg.sum(axis=(0, 1)), do.sum(axis=(0, 1))
     cg, co = np.cumsum(zg) / zg.sum(), np.cumsum(zo) / zo.sum()
     assert np.max(np.abs(cg - co)) < 0.03
-    # lateral extent centred on the entry cell
+    # lateral distributions as the oracle's (rotations of 0-45 deg lean the
+    # beam towards +x and +y: the oracle itself puts ~5 % of the energy in
+    # the outer 8 voxels on the + side)
+    for ax in ((1, 2), (0, 2)):
+        lg, lo = dg.sum(axis=ax), do.sum(axis=ax)
+        assert np.max(np.abs(np.cumsum(lg) / lg.sum() - np.cumsum(lo) / lo.sum())) < 0.03
+    # centred on the entry cell: the outer quarters hold little of it
     xg = dg.sum(axis=(1, 2))
-    assert xg[:8].sum() < 0.05 * xg.sum() and xg[-8:].sum() < 0.05 * xg.sum()
+    assert xg[:8].sum() < 0.1 * xg.sum() and xg[-8:].sum() < 0.1 * xg.sum()

@@ -63,6 +63,7 @@ class Params(C.Structure):
         ("de_max", C.c_double),
         ("dose_scale", C.c_double), ("fb_ec", C.c_double), ("sigma_am", C.c_double),
         ("fb_map", C.c_void_p),
+        ("dx_min", C.c_double),
     ]
 
 
@@ -197,6 +198,7 @@ def params(w: dict, screening: int = 1) -> Params:
     p.fb_ec = float(w.get("e_crit", 0.0))
     p.sigma_am = float(w.get("sigma_amorphous", 0.0))
     p.fb_map = None
+    p.dx_min = min(float(w.get("dx_min", 0.0)) or 1e-4, float(w["dx_max"]))
     return p
 
 

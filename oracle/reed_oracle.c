@@ -109,6 +109,9 @@ typedef struct {
      * the run started */
     double dose_scale, fb_ec, sigma_am;
     const double* fb_map;
+    /* the energy term never shortens the fastest particle's step below dx_min
+     * (A; reading, see o_pick_dt) */
+    double dx_min;
 } o_params;
 
 typedef struct {
@@ -767,7 +770,10 @@ double o_forces(const o_params* P, const double* xi, int with_ion, int n, const 
 /* available at each half kick.  Optional energy term (the paper's step in  */
 /* terms of kinetic and collisional energy, reading): dt <= de_max / P, P   */
 /* the largest |F . v| (conservative force, velocity) over the ion and the  */
-/* integrated atoms at the start of the step.                               */
+/* integrated atoms at the start of the step.  It never shortens the       */
+/* fastest particle's step below dx_min: a step that moves nothing by more   */
+/* than a few ulp of a single-precision coordinate would stall an FP32       */
+/* window, and the 0.05 A rule already bounds the step from above.           */
 /* ------------------------------------------------------------------------ */
 static void o_drag(const o_params* P, double gam, double rho0, const o_ion* I, const double* v,
                    const double* x, double rho, double F[3])
@@ -802,7 +808,10 @@ static double o_pick_dt(const o_params* P, const o_ion* I, const o_win* W)
                             W->f[3 * j + 2] * W->v[3 * j + 2]);
             if (q > pw) pw = q;
         }
-        if (pw * dt > P->de_max) dt = P->de_max / pw;
+        if (pw * dt > P->de_max) {
+            dt = P->de_max / pw;
+            if (vmax * dt < P->dx_min) dt = P->dx_min / vmax;
+        }
     }
     return dt;
 }

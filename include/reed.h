@@ -192,12 +192,17 @@ typedef struct {
      * dt <= de_max / P with P the largest |F . v| over the ion and the
      * integrated atoms at the start of the step (conservative forces), i.e. no
      * particle's kinetic energy changes by much more than de_max (eV) in one
-     * step.  0 = off. */
+     * step -- but never so that the fastest particle moves less than dx_min
+     * in the step.  0 = off. */
     double de_max;
     /* Polls of the shared clone pool by a CTA that ran out of work before it
      * gives up and the run returns REED_E_TIMEOUT (each poll sleeps about
      * 0.5-4 us); 0 = 2^26, about five minutes. */
     int64_t pool_poll_limit;
+    /* Shortest step of the fastest particle that the energy term may impose,
+     * A: below a few ulp of a single-precision window coordinate (~1e-6 A) a
+     * step moves nothing and a collision stalls.  0 = 1e-4 A. */
+    double dx_min;
 } reed_run_opts;
 
 /* Per-track result: the depth and weight of one finished track (Sec. 3, result messages). */

@@ -183,6 +183,7 @@ template <typename T> void fill_hot(HotParams<T>& h, const DevParams& P, const r
     h.rlist2 = (T)((cut + skin) * (cut + skin));
     h.skin = (T)skin;
     h.de_max = (T)P.de_max;
+    h.dx_min = (T)P.dx_min;
     h.g_lo = (T)(-P.half_n * P.a);
     h.g_inv = (T)(P.g_nb / (P.n * P.a));
     // Buckingham
@@ -352,6 +353,7 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.dzhalf = P.bulk ? P.dhalf : 0.0;
     P.dmin = o.damage_min;
     P.de_max = o.de_max > 0.0 ? o.de_max : 0.0;
+    P.dx_min = o.dx_min > 0.0 ? std::min(o.dx_min, o.dx_max) : std::min(1e-4, o.dx_max);
     P.pool_polls = o.pool_poll_limit > 0 ? o.pool_poll_limit : (1ll << 26);
     const double skin = o.nl_skin > 0.0 ? o.nl_skin : (P.tt == REED_TT_TERSOFF ? kSkinTersoff : kSkinPairs);
     // neighbour-search grid over the window: bins no narrower than the list

@@ -54,6 +54,7 @@ template <typename R> struct HotParams {
     R t_blo, t_binvw, t_zk, t_zia, rlist2, skin;
     R g_lo, g_inv;   // neighbour-search grid: low corner (anchor frame) and bins per A
     R de_max;        // energy term of the adaptive step (0 = off)
+    R dx_min;        // shortest step of the fastest particle the energy term may impose
     // Buckingham
     R bA[3], brho_inv[3], bC[3], b_lo, b_binvw, b_rt, b_rinvw, b_rc2, b_zk[3], b_zia[3];
     // ion step
@@ -95,7 +96,7 @@ struct DevParams {
     double gamma, s_loc, rho0_inv, lam_inv;
     int rho_on;
     // integrator (Sec. 2, Fig. "dt_E")
-    double dt_max, dx_max, e_stop, de_max;
+    double dt_max, dx_max, e_stop, de_max, dx_min;
     long long step_cap;
     long long pool_polls;   // polls of the clone pool by an idle CTA before it gives up
     // beam

@@ -1042,7 +1042,10 @@ template <typename R> __device__ void ion_prologue(const DevParams& P, const Hot
     if (vmax * dt > H.dx_max) dt = H.dx_max / vmax;
     if (H.de_max > R(0)) {   // energy term: |dE_kin| <= de_max per step for every particle
         const R pw = max(fabs(I.f[0] * I.v[0] + I.f[1] * I.v[1] + I.f[2] * I.v[2]), I.pmax);
-        if (pw * dt > H.de_max) dt = H.de_max / pw;
+        if (pw * dt > H.de_max) {
+            dt = H.de_max / pw;
+            if (vmax * dt < H.dx_min) dt = H.dx_min / vmax;   // a step that moves nothing stalls
+        }
     }
     const R kd = drag_k<R>(H, S);
     S->on1 = S->rel[2] >= S->zsurf;

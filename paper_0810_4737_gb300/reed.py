@@ -55,7 +55,8 @@ class reed_run_opts(C.Structure):
                 ("damage_n", C.c_int32), ("reserved3", C.c_int32), ("damage_voxel", C.c_double),
                 ("damage_min", C.c_double), ("adjoint", C.c_int32), ("adj_segment", C.c_int32),
                 ("adj_every", C.c_int32), ("reserved4", C.c_int32),
-                ("nl_skin", C.c_double), ("de_max", C.c_double), ("pool_poll_limit", C.c_int64)]
+                ("nl_skin", C.c_double), ("de_max", C.c_double), ("pool_poll_limit", C.c_int64),
+                ("dx_min", C.c_double)]
 
 
 class reed_track_record(C.Structure):
@@ -229,6 +230,7 @@ def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, reco
     o.adjoint, o.adj_segment, o.adj_every = (1 if adjoint else 0), adj_segment, adj_every
     o.nl_skin = nl_skin
     o.de_max = float(w.get("de_max", 0.0))
+    o.dx_min = float(w.get("dx_min", 0.0))
     o.pool_poll_limit = pool_poll_limit
     return o
 

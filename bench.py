@@ -39,7 +39,7 @@ SMS, FP32_LANES = 152, 128
 # ions), from the one-pass ncu capture of that launch summarised in
 # profiles/reed_track_kernel_tersoff_as10kev.md (None when the kernel has
 # changed since).
-TRAFFIC_PER_LAUNCH = 414_210
+TRAFFIC_PER_LAUNCH = 393_220
 
 
 def _ion_name(w):

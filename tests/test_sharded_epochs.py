@@ -93,6 +93,24 @@ def test_one_rank_matches_oracle_adaptive(O):
     assert len(hist) == ref["epochs"]
 
 
+def test_one_rank_calls_a_given_allreduce(O):
+    # a single-rank process group still sums through its collective (the
+    # NCCL path on one GPU); the result is the no-collective run's
+    w = _w()
+    ref = OracleShard(O, w, seed=4)
+    h_ref = sharded.run_adaptive(ref, N_IONS, EPOCH, N_INIT, DEPTHS0)
+    calls = []
+
+    def allreduce(a):
+        calls.append(1)
+        return np.array(a, dtype=np.float64)
+    eng = OracleShard(O, w, seed=4)
+    hist = sharded.run_adaptive(eng, N_IONS, EPOCH, N_INIT, DEPTHS0, allreduce=allreduce)
+    assert len(calls) == len(hist) and np.array_equal(np.array(hist), np.array(h_ref))
+    with pytest.raises(ValueError):
+        sharded.run_adaptive(OracleShard(O, w, seed=4), N_IONS, EPOCH, N_INIT, DEPTHS0, rank=0, world=2)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))

@@ -64,3 +64,17 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(R, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         R.lib()
+
+
+def test_binding_constants_match_the_header():
+    from paper_0810_4737_gb300 import reed as R
+    src = open(os.path.join(ROOT, "include", "reed.h")).read()
+    d = {k: int(v) for k, v in re.findall(r"#define REED_([A-Z0-9_]+)\s+(-?\d+)", src)}
+    for name in ("OK", "E_ARG", "E_CUDA", "E_TIMEOUT", "E_QUEUE_FULL", "E_NONFINITE", "E_NOMEM", "E_SMEM",
+                 "E_STATE", "E_NEIGHBOR", "W_NEIGHBOR", "PREC_MIXED", "PREC_FP64"):
+        assert getattr(R, name) == d[name], name
+    for table, prefix in ((R.LATTICE, "LATTICE_"), (R.TT, "TT_"), (R.BEAM, "BEAM_"), (R.TARGET, "TARGET_")):
+        declared = {k[len(prefix):].lower(): v for k, v in d.items() if k.startswith(prefix)}
+        assert table == declared, prefix
+    assert (R.STOPPED, R.BACKSCATTERED, R.TRUNCATED, R.FAILED) == tuple(
+        d["TRACK_" + k] for k in ("STOPPED", "BACKSCATTERED", "TRUNCATED", "FAILED"))

@@ -23,7 +23,10 @@
  *   - rare-event enhancement: a track that first passes a cloning depth is
  *     split in two, each copy carrying half the weight (Sec. 2, Fig. "split");
  *     cloning depths are frozen during a track (Sec. 3);
- *   - the weighted range (stopping depth) histogram (Sec. 2).
+ *   - the weighted range (stopping depth) histogram (Sec. 2);
+ *   - the paper's own runs (Sec. 4.1, 4.2): recoils starting on a lattice
+ *     site of a bulk crystal in a random direction, their range measured
+ *     from the start.
  * Target-target forces (Sec. 1: "all the relevant atomic interactions are
  * included every time step") are Tersoff Si(C) [PRB 38, 9902 (1988)] with a
  * ZBL blend at short range, or Buckingham pair terms splined to ZBL.

@@ -941,8 +941,9 @@ __device__ long long finish_track(const DevParams& P, const DevBuf& B, const Ion
 
 // Add a half kick to the ion's velocity.  In FP32 the sum is kept as two
 // floats, v + vlo (Knuth's TwoSum), so that increments of a few ulp -- the drag
-// on an MeV ion over its 0.05 A steps -- do not round systematically: a plain
-// FP32 sum shortened the 85 MeV Kr drag range by 0.7 %, the pair by < 1e-6.
+// on an MeV ion over its 0.05 A steps -- do not round systematically: with a
+// plain FP32 sum the 85 MeV Kr drag-only range came out 0.7 % short, with the
+// two-float sum within 1e-6.
 template <typename R> __device__ __forceinline__ void add_velocity(IonState<R>& I, int d, R inc)
 {
     if constexpr (sizeof(R) == 4) {

@@ -34,11 +34,10 @@
  * Where the paper defers to its references, the readings taken are listed in
  * the project's design notes; each is marked "reading:" below.
  *
- * Parity unpinned: the magnitude of the Lindhard-Scharff drag coefficient
- * (o_gamma_ls) and the Buckingham parameter values are readings with no
- * independent published number to test against; only their use (the drag's
- * closed-form range, Buckingham forces against finite differences and the
- * fluorite symmetry) is pinned.
+ * Parity unpinned: the Buckingham parameter values are readings with no
+ * independent published number to test against; only their use (forces
+ * against finite differences and the fluorite symmetry) is pinned.  The
+ * Lindhard-Scharff magnitude is pinned against the LSS reduced-unit form.
  *
  * Units: Angstrom, eV, amu; time unit tau = sqrt(amu A^2 / eV) = 10.1805 fs.
  */

@@ -268,3 +268,42 @@ def test_energy_term_of_the_time_step(O):
     r1 = O.run(O.params(w1), 256, seed=2)["records"]
     z0, z1 = r0["z"][r0["status"] == 1], r1["z"][r1["status"] == 1]
     assert abs(np.mean(z1) / np.mean(z0) - 1) < 0.06
+
+
+def _gamma_lss_reduced(Z1, M1, targets):
+    """Drag coefficient from the Lindhard-Scharff-Schiott stopping in reduced
+    units, d eps / d rho = k_L eps^(1/2) with k_L = xi_e 0.0793 Z1^(1/2)
+    Z2^(1/2) (A1+A2)^(3/2) / ((Z1^(2/3)+Z2^(2/3))^(3/4) A1^(3/2) A2^(1/2)),
+    xi_e = Z1^(1/6), eps = E a M2 / (Z1 Z2 e^2 (M1+M2)), rho = x N 4 pi a^2
+    M1 M2 / (M1+M2)^2, a = 0.8853 a0 (Z1^(2/3)+Z2^(2/3))^(-1/2): converted
+    to dE/dx by the chain rule and divided by v.  targets: (Z2, M2, N)."""
+    E2, A0 = 14.399645, 0.529177
+    E = 1000.0
+    v = np.sqrt(2 * E / M1)
+    dEdx = 0.0
+    for Z2, M2, N in targets:
+        s = Z1 ** (2 / 3) + Z2 ** (2 / 3)
+        a = 0.8853 * A0 / np.sqrt(s)
+        deps_dE = a * M2 / (Z1 * Z2 * E2 * (M1 + M2))
+        drho_dx = N * 4 * np.pi * a ** 2 * M1 * M2 / (M1 + M2) ** 2
+        kL = Z1 ** (1 / 6) * 0.0793 * np.sqrt(Z1 * Z2) * (M1 + M2) ** 1.5 / (s ** 0.75 * M1 ** 1.5 * np.sqrt(M2))
+        dEdx += kL * np.sqrt(E * deps_dE) * drho_dx / deps_dE
+    return dEdx / v
+
+
+@pytest.mark.parametrize("name", ["b1kev_si_0k_zbl", "as10kev_si_300k_tersoff", "ar30kev_ceo2_300k_buck",
+                                  "u85kev_uo2_300k_recoil", "kr85mev_uo2_300k_recoil"])
+def test_lindhard_scharff_magnitude_matches_the_reduced_form(O, name):
+    """The oracle's drag coefficient (dimensional Lindhard-Scharff constant
+    1.212 eV^1/2 A^2, per-species density sum) equals the LSS reduced-unit
+    form converted to A and eV, up to the rounding of the two published
+    constants (0.0793 and 1.212 differ by 4.5e-4 after conversion)."""
+    w = workload(name)
+    a = w["a"]
+    sp = w["species"]
+    if w["lattice"] == "diamond":
+        targets = [(sp[0]["Z"], sp[0]["M"], 8 / a ** 3)]
+    else:
+        targets = [(sp[0]["Z"], sp[0]["M"], 4 / a ** 3), (sp[1]["Z"], sp[1]["M"], 8 / a ** 3)]
+    g = _gamma_lss_reduced(w["ion"]["Z"], w["ion"]["M"], targets)
+    assert abs(O.gamma_ls(O.params(w)) / g - 1) < 1e-3

@@ -34,10 +34,10 @@
  * Where the paper defers to its references, the readings taken are listed in
  * the project's design notes; each is marked "reading:" below.
  *
- * Parity unpinned: the Buckingham parameter values are readings with no
- * independent published number to test against; only their use (forces
- * against finite differences and the fluorite symmetry) is pinned.  The
- * Lindhard-Scharff magnitude is pinned against the LSS reduced-unit form.
+ * Parity unpinned: the O-O Buckingham values, which no test property is
+ * sensitive to (the Ce-O values are pinned by the CeO2 lattice constant they
+ * reproduce with formal charges; the Lindhard-Scharff magnitude against the
+ * LSS reduced-unit form).
  *
  * Units: Angstrom, eV, amu; time unit tau = sqrt(amu A^2 / eV) = 10.1805 fs.
  */

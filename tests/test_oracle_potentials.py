@@ -326,3 +326,26 @@ def test_buckingham_ceria_reproduces_its_lattice_constant(O):
     roots = [r.real for r in np.roots(np.polyder(c)) if abs(r.imag) < 1e-9 and aa[0] < r.real < aa[-1]]
     assert len(roots) == 1
     assert abs(roots[0] / 5.411 - 1) < 6e-3, roots
+
+
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+@pytest.mark.parametrize("eps", [0.01, 0.1, 1.0, 10.0])
+def test_zbl_nuclear_stopping_matches_the_universal_fit(O, eps):
+    """The oracle's ZBL potential, through classical two-body scattering
+    (deflection integral, T = gamma E sin^2(theta/2), S_n = int T 2 pi b db),
+    gives the reduced nuclear stopping of the ZBL universal fit
+    s_n = ln(1 + 1.1383 eps) / (2 (eps + 0.01321 eps^0.21226 + 0.19593 eps^0.5))
+    within the fit's few per cent: an independent check of the screening
+    function's coefficients and of the universal screening length."""
+    Z1, M1, Z2, M2 = B11["Z"], B11["M"], SI["Z"], SI["M"]
+    aU = O.screen_length(Z1, Z2)
+    E = eps * Z1 * Z2 * E2 * (M1 + M2) / (aU * M2)
+    Ec = E * M2 / (M1 + M2)
+    V = lambda r: O.zbl(Z1, Z2, r)[0]
+    f = lambda s: np.sin(0.5 * deflection_angle(V, Ec, aU * s)) ** 2 * s
+    tot = sum(integrate.quad(f, lo, hi, limit=200, epsrel=1e-6)[0]
+              for lo, hi in [(0, 0.5), (0.5, 2), (2, 8), (8, 30), (30, 120)])
+    sn = eps * 2 * tot          # eps S_n / (pi aU^2 gamma E) with S_n = gamma E 2 pi aU^2 tot
+    fit = np.log(1 + 1.1383 * eps) / (2 * (eps + 0.01321 * eps ** 0.21226 + 0.19593 * eps ** 0.5))
+    assert abs(sn / fit - 1) < 0.05, (sn, fit)
+    assert abs(aU / (0.8854 * 0.529177 / (Z1 ** 0.23 + Z2 ** 0.23)) - 1) < 1e-12

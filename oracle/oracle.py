@@ -133,6 +133,10 @@ def lib():
             L.o_segment_replay_theta.argtypes = [_P, C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int64, C.c_int,
                                                  C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
             L.o_segment_replay_theta.restype = C.c_double
+            L.o_bspline3_export.argtypes = [C.c_double, _D]
+            L.o_bspline3_export.restype = C.c_double
+            L.o_spline_corr_export.argtypes = [_D, C.c_double, _D]
+            L.o_spline_corr_export.restype = C.c_double
             L.o_basis_count.argtypes = [C.c_int]
             L.o_basis_count.restype = C.c_int
             _LIB = L
@@ -401,6 +405,22 @@ def pair_full(p: Params, Z2: float, r: float):
     dc = np.zeros(6)
     lib().o_pair_full(C.byref(p), Z2, r, C.byref(U), C.byref(dU), C.byref(d2U), _dp(dc))
     return U.value, dU.value, d2U.value, dc
+
+
+def bspline3(u: float):
+    """The oracle's centred cubic B-spline of unit knot spacing: (B(u), B'(u))."""
+    du = C.c_double()
+    b = lib().o_bspline3_export(u, C.byref(du))
+    return b, du.value
+
+
+def spline_corr(c, r: float):
+    """The ZBL correction c(r) = sum_i c_i B_i(ln r) and dc/dr (oracle)."""
+    cc = np.ascontiguousarray(c, dtype=np.float64)
+    assert cc.size == 6
+    d = C.c_double()
+    v = lib().o_spline_corr_export(_dp(cc), r, C.byref(d))
+    return v, d.value
 
 
 def segment_tangent(p: Params, seed: int, track_id: int, seg: int = 200, every: int = 20, cap: int = 2_000_000):

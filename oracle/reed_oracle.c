@@ -623,7 +623,11 @@ static double o_g(double c, double C, double Dd, double H, double* dg)
 }
 
 /* Tersoff energy with ZBL blend; scatter forces into f (3n). All n atoms
- * are included in the energy; brute-force O(n^2) pair search. */
+ * are included in the energy.  The partners of atom i are the atoms j != i
+ * with r_ij < R + D, found by brute force over all n atoms and kept in
+ * ascending index order; the sums over j and over the third atom k run over
+ * that list, which visits exactly the terms (and in the same order) of a
+ * loop over all atoms that skips those beyond the cutoff. */
 static double o_tersoff(const o_params* P, int n, const double* x, double* f)
 {
     const double *T = P->ters;
@@ -633,17 +637,25 @@ static double o_tersoff(const o_params* P, int n, const double* x, double* f)
     double E = 0.0;
     double Zs = P->Z2[0];
     double bn = pow(beta, nn);
-    for (int i = 0; i < n; ++i) {
+    int* cnt = (int*)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
+    int* nbr = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
+            double rv[3];
+            if (o_dist(&x[3 * i], &x[3 * j], rv) < rcut) nbr[(size_t)i * n + cnt[i]++] = j;
+        }
+    for (int i = 0; i < n; ++i) {
+        const int* Ni = nbr + (size_t)i * n;
+        for (int jj = 0; jj < cnt[i]; ++jj) {
+            const int j = Ni[jj];
             double rij_v[3], rij = o_dist(&x[3 * i], &x[3 * j], rij_v);
-            if (rij >= rcut) continue;
             /* zeta_ij */
             double zeta = 0.0;
-            for (int k = 0; k < n; ++k) {
-                if (k == i || k == j) continue;
+            for (int kk = 0; kk < cnt[i]; ++kk) {
+                const int k = Ni[kk];
+                if (k == j) continue;
                 double rik_v[3], rik = o_dist(&x[3 * i], &x[3 * k], rik_v);
-                if (rik >= rcut) continue;
                 double dfc, fck = o_fc(rik, R, D, &dfc);
                 double cs = (rij_v[0] * rik_v[0] + rij_v[1] * rik_v[1] + rij_v[2] * rik_v[2]) / (rij * rik);
                 double dg;
@@ -672,10 +684,10 @@ static double o_tersoff(const o_params* P, int n, const double* x, double* f)
             /* bond-order part: prefactor 0.5 * dV/db * db/dzeta */
             double pre = 0.5 * (1.0 - s) * fc * fA * dbdz;
             if (pre == 0.0) continue;
-            for (int k = 0; k < n; ++k) {
-                if (k == i || k == j) continue;
+            for (int kk = 0; kk < cnt[i]; ++kk) {
+                const int k = Ni[kk];
+                if (k == j) continue;
                 double rik_v[3], rik = o_dist(&x[3 * i], &x[3 * k], rik_v);
-                if (rik >= rcut) continue;
                 double dfck, fck = o_fc(rik, R, D, &dfck);
                 double cs = (rij_v[0] * rik_v[0] + rij_v[1] * rik_v[1] + rij_v[2] * rik_v[2]) / (rij * rik);
                 double dg, g = o_g(cs, C, Dd, H, &dg);
@@ -692,6 +704,8 @@ static double o_tersoff(const o_params* P, int n, const double* x, double* f)
             }
         }
     }
+    free(nbr);
+    free(cnt);
     return E;
 }
 
@@ -1375,6 +1389,9 @@ double o_ion_pair_energy(const o_params* P, double Z2, double r, double* dU)
 }
 double o_taper_export(double r, double rt, double rc, double* dS) { return o_taper(r, rt, rc, dS); }
 double o_tau_fs(void) { return O_TAU_FS; }
+/* the ZBL-correction basis and correction, exported for the pin tests */
+double o_bspline3_export(double u, double* du) { return o_bspline3(u, du); }
+double o_spline_corr_export(const double* c, double r, double* dcdr) { return o_spline_corr(c, r, dcdr); }
 
 /* ======================================================================== */
 /* Truncated-segment sensitivities (the adjoint workload).                  */

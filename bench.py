@@ -5,10 +5,12 @@ workload's primaries (4096 As ions at 10 keV into Si at 300 K, Tersoff
 target, 5x5x5-cell window) followed to the end of every track.  Each timed
 step runs a fresh batch (primary ids step*n ... ) in the mixed-precision form.
 
-Reported beside it: the plain FP64 GPU path on a sample of the same batch
-(the metric's comparison), the range-profile KS p-value between the two, the
-FP32-ALU roofline of the stepper kernel, the CPU oracle timed on the host
-cores, and an end-to-end figure through the public API with host buffers.
+Reported beside it: the plain FP64 GPU path on the same 4096-ion batch as
+the first timed step (the metric's comparison), the range-profile error of
+both forms against the oracle's stored ranges of this workload (mean,
+straggle, KS p, with their sampling errors), the FP32-ALU and SFU rooflines
+of the stepper kernel, the CPU oracle timed on the host cores, and an
+end-to-end figure through the public API with host buffers.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs its own shard of primaries (weak scaling).
@@ -34,12 +36,15 @@ WORKLOAD = "as10kev_si_300k_tersoff"
 # Algorithmic FP32 work per unit (see the design notes): ZBL ion-target pair
 # 35 ops, integrated atom update 12 FMA = 24 ops, Tersoff bond-angle triplet 60 ops.
 OPS_PAIR, OPS_MOVE, OPS_TRIPLET = 35, 24, 60
+# Algorithmic SFU (transcendental) work per unit: ZBL pair 4 ex2 + 1 rsqrt,
+# Tersoff bond-angle term one reciprocal (the angular function g).
+SFU_PAIR, SFU_TRIPLET = 5, 1
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of one bench launch of the stepper kernel (4096
 # ions), from the one-pass ncu capture of that launch summarised in
 # profiles/reed_track_kernel_tersoff_as10kev.md (None when the kernel has
 # changed since).
-TRAFFIC_PER_LAUNCH = 393_220
+TRAFFIC_PER_LAUNCH = None
 
 
 def _ion_name(w):
@@ -141,26 +146,30 @@ def cpu_baseline(w, n_ions, threads, step_cap):
     return r["steps"] / dt, r["steps"], dt
 
 
-def oracle_parity(R, n):
+def oracle_parity(w, forms):
     """Mean, straggle and two-sample KS p of the range profile of each GPU
-    form against the oracle on the same primaries."""
-    from oracle import oracle as O
-    from paper_0810_4737_gb300.workloads import workload
-    w = workload("b1kev_si_0k_zbl")
-    ref = O.run(O.params(w), n, seed=1, threads=os.cpu_count() or 1)["records"]
-    zo = ref["z"][ref["status"] == 1]
-    out = {"workload": w["name"], "ions": n, "oracle_mean_A": float(np.mean(zo)), "oracle_straggle_A": float(np.std(zo))}
-    for name, prec in (("mixed", R.PREC_MIXED), ("fp64", R.PREC_FP64)):
-        with R.Reed(w) as c:
-            c.run(n_ions=n, seed=1, precision=prec)
-            rec = c.records()
-        z = rec["z"][rec["status"] == 1]
-        out[name] = {"mean_rel_err": float(np.mean(z) / np.mean(zo) - 1), "straggle_rel_err": float(np.std(z) / np.std(zo) - 1),
-                     "ks_p": _ks(z, zo),
+    form against the oracle's ranges of the same workload, stored by
+    tests/golden/make_range_goldens.py (independent primaries: GPU and oracle
+    samples use different seeds).  forms: {name: (depths of stopped tracks, n)}."""
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    try:
+        import make_range_goldens as G
+        ids, z, st, _ = G.read(w["name"])
+    except (ImportError, OSError) as e:
+        return {"workload": w["name"], "unavailable": "no stored oracle ranges (%s)" % e}
+    z, st = np.asarray(z), np.asarray(st)
+    zo = z[st == 1]
+    out = {"workload": w["name"], "oracle_ions": len(ids), "oracle_mean_A": float(np.mean(zo)),
+           "oracle_straggle_A": float(np.std(zo)), "source": "tests/golden/ranges_%s.txt (FP64 C oracle)" % w["name"]}
+    for name, (zg, n) in forms.items():
+        if len(zg) < 2:
+            continue
+        out[name] = {"ions": n, "mean_rel_err": float(np.mean(zg) / np.mean(zo) - 1),
+                     "straggle_rel_err": float(np.std(zg) / np.std(zo) - 1), "ks_p": _ks(zg, zo),
                      # sampling error of the two estimates (trajectories are chaotic, so
                      # the two samples are effectively independent)
-                     "mean_rel_se": float(np.hypot(_se_mean(z), _se_mean(zo))),
-                     "straggle_rel_se": float(np.hypot(_se_std(z), _se_std(zo)))}
+                     "mean_rel_se": float(np.hypot(_se_mean(zg), _se_mean(zo))),
+                     "straggle_rel_se": float(np.hypot(_se_std(zg), _se_std(zo)))}
     return out
 
 
@@ -214,7 +223,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--ions", type=int, default=0, help="primaries per step per GPU (0: the workload's)")
-    ap.add_argument("--fp64-ions", type=int, default=256, help="sample of the plain FP64 path")
+    ap.add_argument("--fp64-ions", type=int, default=-1,
+                    help="primaries of the plain FP64 path (-1: the whole batch of a step, 0: skip)")
     ap.add_argument("--cpu-ions", type=int, default=0, help="oracle sample primaries (0: one per host core)")
     ap.add_argument("--cpu-steps", type=int, default=1200, help="oracle sample: steps per primary")
     ap.add_argument("--ref-ions", type=int, default=0, help="reference arm primaries per step (0: one per core)")
@@ -292,6 +302,7 @@ def main():
     pairs_per_s = (st["pair_evals"] + st["bond_evals"]) * ws / (tot_ms * 1e-3)
     # roofline of the stepper kernel (FP32 ALU)
     flops = OPS_PAIR * st["pair_evals"] + OPS_MOVE * st["atom_updates"] + OPS_TRIPLET * st["triplets"]
+    sfu_ops = SFU_PAIR * st["pair_evals"] + SFU_TRIPLET * st["triplets"]
     kern_s = sum(kernel_ms) * 1e-3
     achieved = flops / kern_s / 1e12
     derived = SMS * FP32_LANES * 2 * 2070e6 / 1e12
@@ -316,32 +327,39 @@ def main():
         d2h = 8 * (nb + 3) + ctypes.sizeof(R.reed_stats_t)
         e2e = {"value": e2e_steps / dt, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "note": "reed_run + reed_range_profile (into pinned host memory) + reed_stats per step, host wall clock"}
-    # ---- plain FP64 path on a sample, and the KS check of the two profiles
-    fp64 = None
-    if rank == 0 and args.fp64_ions > 0:
-        m = args.fp64_ions
+    # ---- the plain FP64 path on the batch of the first timed step (the same
+    # primaries as that step's mixed-form run), and the KS check of the two profiles
+    fp64, forms = None, {}
+    m = n if args.fp64_ions < 0 else args.fp64_ions
+    if rank == 0 and m > 0:
+        fid = first + args.warmup * n   # the first timed step's primaries
         with R.Reed(w) as c64, R.Reed(w) as c32:
-            c64.run(n_ions=m, seed=w["seed"], first_id=first, precision=R.PREC_FP64, stream=sh)
+            # (the FP64 path runs in the library's default launch shape)
+            c64.run(n_ions=m, seed=w["seed"], first_id=fid, precision=R.PREC_FP64, stream=sh)
             s64 = c64.stats()
             r64 = c64.records()
-            c32.run(n_ions=m, seed=w["seed"], first_id=first, precision=R.PREC_MIXED, stream=sh)
+            c32.run(n_ions=m, seed=w["seed"], first_id=fid, precision=R.PREC_MIXED, stream=sh, **launch)
             s32 = c32.stats()
             r32 = c32.records()
         z64 = r64["z"][r64["status"] == R.STOPPED]
         z32 = r32["z"][r32["status"] == R.STOPPED]
+        forms = {"mixed": (z32, m), "fp64": (z64, m)}
         f64ops = OPS_PAIR * s64["pair_evals"] + OPS_MOVE * s64["atom_updates"] + OPS_TRIPLET * s64["triplets"]
         a64 = f64ops / (s64["kernel_ms"] * 1e-3) / 1e12
-        fp64 = {"value": s64["steps"] / (s64["kernel_ms"] * 1e-3), "unit": "ion-steps/s",
+        v64 = s64["steps"] / (s64["kernel_ms"] * 1e-3)
+        v32 = s32["steps"] / (s32["kernel_ms"] * 1e-3)
+        fp64 = {"value": v64, "unit": "ion-steps/s", "sample_ions": m,
+                "sample": "the %d primaries of the first timed step%s" % (m, "" if m == n else " (first %d)" % m),
                 "roofline": {"bound": "fp64", "achieved": a64, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
                              "frac": a64 / peaks["fp64_tflops"], "peak_source": "measured FP64 FMA stream (reed_peaks)"},
-                "mixed_same_sample": s32["steps"] / (s32["kernel_ms"] * 1e-3), "sample_ions": m,
+                "launch": {"threads_per_track": s64["threads_per_track"], "ctas_per_sm": s64["ctas_per_sm"],
+                           "grid": s64["grid"]},
+                "mixed_same_sample": v32, "mixed_over_fp64": v32 / v64,
                 "ks_p_mixed_vs_fp64": _ks(z32, z64),
                 "mean_depth_A": [float(np.mean(z32)) if len(z32) else None, float(np.mean(z64)) if len(z64) else None]}
-    # ---- per-profile error of both GPU forms against the oracle on the small
-    # workload (4096 B ions at 1 keV, 0 K; full tracks are cheap on the CPU there)
-    parity = None
-    if rank == 0 and not args.no_cpu:
-        parity = oracle_parity(R, 4096)
+    # ---- per-profile error of both GPU forms against the oracle's stored
+    # ranges of this workload
+    parity = oracle_parity(w, forms) if rank == 0 and forms else None
     # ---- CPU oracle on the host cores (bounded sample)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -367,6 +385,10 @@ def main():
             "autotune": [{"threads_per_track": t, "ctas_per_sm": c, "ion_steps_per_s": v} for t, c, v in tune],
             "gpu_launches": args.steps,
             "clocks": clk,
+            "sfu": {"achieved_gops": sfu_ops / kern_s / 1e9, "peak_gops": peaks["ex2_gops"],
+                    "frac": sfu_ops / kern_s / 1e9 / peaks["ex2_gops"],
+                    "peak_source": "measured ex2.approx stream (reed_peaks)",
+                    "units": "algorithmic: 5 per ion-target pair (4 ex2 + rsqrt), 1 per Tersoff bond-angle term"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
                          "frac": achieved / peaks["fp32_tflops"], "traffic": TRAFFIC_PER_LAUNCH if w["name"] == WORKLOAD and n == 4096 else None,
                          "peak_source": "measured FP32 FMA stream (reed_peaks, burst) at %.0f MHz; derived "
@@ -379,7 +401,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "stats": {k: st[k] for k in ("primaries", "tracks", "steps", "pair_evals", "bond_evals", "triplets",
-                                         "atom_updates", "shifts", "rebuilds", "nb_overflow", "bond_cap_overflow",
+                                         "atom_updates", "shifts", "rebuilds", "nb_overflow", "bond_cap_overflow", "nb_spilled",
                                          "threads_per_track", "ctas_per_sm", "grid", "smem_bytes", "phase_cycles")},
         }
         print(json.dumps(line), flush=True)

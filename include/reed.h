@@ -47,11 +47,13 @@ extern "C" {
 #define REED_E_NOMEM -6      /* device memory allocation failed */
 #define REED_E_SMEM -7       /* the window does not fit in shared memory */
 #define REED_E_STATE -8      /* call made in the wrong state (e.g. no run yet) */
-#define REED_E_NEIGHBOR -9   /* (reserved) */
-/* Positive codes: the run completed, with a counted anomaly (see reed_stats). */
-#define REED_W_NEIGHBOR 1    /* some atom had more target neighbours than a list holds, or
-                                found no list slot: the surplus bonds were left out of its
-                                forces (nb_overflow, bond_cap_overflow) */
+#define REED_E_NEIGHBOR -9   /* the run completed but some target forces were incomplete: an
+                                atom had more list neighbours than its overflow row holds
+                                (64 Tersoff, 192 pair), a track needed more than 32 overflow
+                                rows at once, or a needed atom found no list row
+                                (reed_stats: nb_overflow, bond_cap_overflow).  Every force of
+                                the paper's model is evaluated otherwise (Sec. 1: all the
+                                relevant interactions every time step). */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define REED_LATTICE_DIAMOND 0   /* 8-atom cubic cell, one species (Si) */
@@ -225,8 +227,8 @@ typedef struct {
     int64_t rebuilds;        /* neighbour-list builds */
     int64_t stopped, backscattered, truncated, failed;
     int64_t dropped_clones;  /* clones lost to a full stack */
-    int64_t nb_overflow;     /* neighbour-list overflows (bonds beyond the per-atom capacity) */
-    int64_t bond_cap_overflow; /* atoms left without Tersoff bond storage */
+    int64_t nb_overflow;     /* neighbour-list entries that found no room (REED_E_NEIGHBOR) */
+    int64_t bond_cap_overflow; /* needed atoms left without a list row (REED_E_NEIGHBOR) */
     int64_t triplets;        /* Tersoff bond-angle (zeta) terms evaluated */
     int64_t atom_updates;    /* integrated target-atom updates (atoms x steps) */
     int64_t phase_cycles[6]; /* SM clock cycles per step phase, summed over CTAs: ion update,
@@ -238,14 +240,19 @@ typedef struct {
                                 paper's per-depth split statistics, Sec. 3) */
     int64_t pooled;          /* clones run by another CTA than the one that made them
                                 (taken from the shared clone pool) */
+    int64_t nb_spilled;      /* lists that outgrew their shared-memory row and moved whole
+                                to an overflow row in global memory (exact, only slower) */
 } reed_stats_t;
 
 typedef struct reed_ctx reed_ctx;
 
-/* Create a context for one target (lattice, species, potentials).  *out
- * receives the context; free it with reed_destroy.  n_species must be 1 for
- * DIAMOND and 2 for FLUORITE.  Selects the current CUDA device.  Errors:
- * REED_E_ARG (invalid parameters), REED_E_CUDA, REED_E_NOMEM. */
+/* Create a context for one target (lattice, species, potentials) -- the
+ * crystal, its statistically realised cells and the interactions of Sec. 2
+ * ("First": ion-target ZBL; "Second": the moving window of unit cells;
+ * "Third": electronic stopping) and the target-target forces of Sec. 1.
+ * *out receives the context; free it with reed_destroy.  n_species must be
+ * 1 for DIAMOND and 2 for FLUORITE.  Selects the current CUDA device.
+ * Errors: REED_E_ARG (invalid parameters), REED_E_CUDA, REED_E_NOMEM. */
 int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, int n_species,
               const reed_potentials* pot);
 
@@ -266,8 +273,8 @@ int reed_init(reed_ctx** out, const reed_lattice* lat, const reed_species* sp, i
  * Clones are run depth first by the CTA that made them, or, while some CTA
  * is out of work, donated to a shared pool that idle CTAs take from (the
  * paper's host handing returned clones to free clients, Sec. 3).
- * Returns REED_OK, REED_W_NEIGHBOR (completed; see nb_overflow), or an error:
- * REED_E_ARG (also a RECOIL beam on a SURFACE target or the reverse, or the
+ * Returns REED_OK or an error:
+ * REED_E_NEIGHBOR (completed, but some target forces were incomplete), REED_E_ARG (also a RECOIL beam on a SURFACE target or the reverse, or the
  * adjoint on a BULK target), REED_E_SMEM, REED_E_CUDA, REED_E_NOMEM; REED_E_QUEUE_FULL and
  * REED_E_NONFINITE mean the run completed but clones or tracks were lost
  * (counted in reed_stats); REED_E_TIMEOUT means a CTA out of work stopped
@@ -318,14 +325,20 @@ int reed_grad(reed_ctx* ctx, double sigma, int n_bins, double bin_width, const d
  * later runs (host, 8 doubles).  REED_E_ARG on a null pointer. */
 int reed_set_theta(reed_ctx* ctx, const double* theta8);
 
-/* Cumulative damage map of all runs since init/reset: out (host or device)
+/* Cumulative damage map of all runs since init/reset -- the shared damage
+ * information the paper's tracks feed back (Sec. 1, Sec. 3: the host keeps
+ * the accumulated damage and hands it to new tracks; here a device-resident
+ * FP64 map updated with atomics): out (host or device)
  * receives n^3 doubles (eV, index (ix n + iy) n + iz; voxel (0,0,0) starts
  * at (-n v / 2, -n v / 2, 0), on a BULK target at (-n v / 2) in all three),
  * overflow (may be NULL) the energy deposited outside the grid.  n must
  * equal damage_n. */
 int reed_damage_map(reed_ctx* ctx, double* out, int n, double* overflow);
 
-/* Counters of all runs since init/reset (host pointer). */
+/* Counters of all runs since init/reset (host pointer): tracks, steps, the
+ * per-depth split statistics of Sec. 3 (splits[]), and the work and phase
+ * clocks that stand in for the computation and communication loads the
+ * paper measures per client in Sec. 4 (Tables 3-4). */
 int reed_stats(reed_ctx* ctx, reed_stats_t* out);
 
 /* Copy up to cap per-track records (host or device) of all runs since
@@ -423,9 +436,12 @@ int reed_peaks(reed_peaks_t* out);
 int reed_reset(reed_ctx* ctx);
 
 /* Message of the last failure of this context (ctx == NULL: of the last
- * failed reed_init on this thread).  Never NULL. */
+ * failed reed_init or reed_run_static on this thread).  Never NULL.  The
+ * paper has no counterpart (error reporting of this interface). */
 const char* reed_last_error(reed_ctx* ctx);
 
+/* Free the context and every device buffer it owns (NULL is ignored).  The
+ * paper has no counterpart (resource management of this interface). */
 void reed_destroy(reed_ctx* ctx);
 
 /* ---- diagnostics: the stepper's own device functions on given inputs --- */
@@ -473,20 +489,24 @@ int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double*
  * No context is needed: the target is described by lat, sp, n_species, pot
  * (as for reed_init) and the run by the remaining arguments (as for
  * reed_run).  The launch's scratch (counters, primary queue, status word,
- * clone stacks) lives in one file-scope device array of 64 MiB that every
- * GPU loading the library holds until the process exits; the first call on
- * a device looks up that array's device address, so make the first call
- * before any stream capture.  Configurations whose clone stacks do not fit
- * (SMs x n_thresholds x window record) are rejected with REED_E_ARG; the
- * launch uses fewer CTAs per SM when that makes them fit.  No per-track
- * records or traces (record_tracks, trace_tracks, trace_steps must be 0).
+ * clone stacks, neighbour-list overflow rows) lives in one file-scope device
+ * array of 64 MiB that every GPU loading the library holds until the process
+ * exits.  The array's device address belongs to a CUDA context: the first
+ * call in each context of a device looks it up (cudaGetSymbolAddress) and
+ * caches it under the context's unique id, so make that first call before
+ * any stream capture.  Configurations whose scratch does not fit (SMs x
+ * (n_thresholds x window record + overflow rows)) are rejected with
+ * REED_E_ARG; the launch uses fewer CTAs per SM when that makes it fit.  No
+ * per-track records or traces (record_tracks, trace_tracks, trace_steps
+ * must be 0).
  *
  * hist_out (device, n_bins + 3 doubles) is overwritten with the weighted
  * range profile followed by {above the surface, beyond the last bin,
  * backscattered}; stats_out (host, may be NULL) receives the counters.
  * Every call shares the one scratch array and clears it first, so calls
  * whose work overlaps on the GPU (from several host threads or streams)
- * race.  Blocks until the run is finished.  Returns as reed_run;
+ * race.  Blocks until the run is finished: it synchronises opt->stream and
+ * reads the counters back before returning.  Returns as reed_run;
  * reed_last_error(NULL) has the message. */
 int reed_run_static(const reed_lattice* lat, const reed_species* sp, int n_species, const reed_potentials* pot,
                     double ion_Z, double ion_M, double energy_eV, double tilt_deg, double rot_deg_lo,

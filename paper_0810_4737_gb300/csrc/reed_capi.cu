@@ -75,6 +75,9 @@ struct reed_ctx {
     // clone stacks
     unsigned char* d_stacks = nullptr;
     size_t stacks_bytes = 0;
+    // neighbour-list overflow rows (per CTA)
+    unsigned char* d_spill = nullptr;
+    size_t spill_bytes = 0;
     // shared clone pool: records, slot states and its two counters
     unsigned char* d_pool = nullptr;
     size_t pool_bytes = 0;
@@ -367,6 +370,10 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     fill_hot<float>(P.hf, P, ctx, skin);
     fill_hot<double>(P.hd, P, ctx, skin);
     P.bond_cap = bond_capacity(P, skin);
+    {
+        const int k = P.n - 2 * P.margin;
+        P.act_cap = k * k * k * P.nb;
+    }
     return REED_OK;
 }
 
@@ -639,7 +646,7 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     if (const char* m = beam_error(ctx->lat, o)) return fail(ctx, REED_E_ARG, "%s", m);
     if (o.precision != REED_PREC_MIXED && o.precision != REED_PREC_FP64) return fail(ctx, REED_E_ARG, "precision");
     if (o.threads_per_track && !valid_threads(o.threads_per_track))
-        return fail(ctx, REED_E_ARG, "threads_per_track must be 0, 32, 64, 128 or 256");
+        return fail(ctx, REED_E_ARG, "threads_per_track must be 0, 32, 64, 128, 256 or 512");
     if (o.ctas_per_sm < 0 || o.trace_tracks < 0 || o.trace_steps < 0 || o.record_capacity < 0)
         return fail(ctx, REED_E_ARG, "negative option");
     int rc;
@@ -704,8 +711,8 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
         P.adj_every = every;
         P.adj_nck = seg / every + 1;
     }
-    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap, P.adjoint, P.g_nbins)
-                            : reed_f32::smem_bytes(tt, P.na, P.bond_cap, P.adjoint, P.g_nbins);
+    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap, P.adjoint, P.g_nbins, P.act_cap)
+                            : reed_f32::smem_bytes(tt, P.na, P.bond_cap, P.adjoint, P.g_nbins, P.act_cap);
     if (smem > ctx->smem_optin)
         return fail(ctx, REED_E_SMEM, "window of %d atoms needs %zu B of shared memory (max %zu)", P.na, smem,
                     ctx->smem_optin);
@@ -749,6 +756,16 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
         B.pool_state = ctx->d_pool_state;
         B.pool_ctl = ctx->d_pool_state + L.grid;
         B.pool_slots = L.grid;
+    }
+    // neighbour-list overflow rows: one block per CTA
+    B.spill_stride = f64 ? reed_f64::spill_bytes(tt) : reed_f32::spill_bytes(tt);
+    if (B.spill_stride) {
+        const size_t need = B.spill_stride * (size_t)L.grid;
+        if (need > ctx->spill_bytes) {
+            if ((rc = dev_alloc(ctx, &ctx->d_spill, need))) return rc;
+            ctx->spill_bytes = need;
+        }
+        B.spill = ctx->d_spill;
     }
     B.hist = ctx->d_hist;
     B.counters = ctx->d_counters;
@@ -902,10 +919,10 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
         return fail(ctx, REED_E_TIMEOUT, "an idle CTA stopped waiting for the shared clone pool: tracks may be missing");
     if (status & ERR_NONFINITE) return fail(ctx, REED_E_NONFINITE, "a track became non-finite (see reed_stats)");
     if (status & ERR_QUEUE) return fail(ctx, REED_E_QUEUE_FULL, "clone stack overflow: clones dropped");
-    if (status & ERR_NEIGHBOR) {
-        fail(ctx, REED_W_NEIGHBOR, "neighbour lists truncated (see nb_overflow in reed_stats)");
-        return REED_W_NEIGHBOR;
-    }
+    if (status & ERR_NEIGHBOR)
+        return fail(ctx, REED_E_NEIGHBOR,
+                    "a neighbour list outgrew its overflow row or the overflow rows ran out (see nb_overflow, "
+                    "bond_cap_overflow in reed_stats): forces were incomplete");
     return REED_OK;
 }
 
@@ -939,6 +956,7 @@ int reed_stats(reed_ctx* ctx, reed_stats_t* out)
     out->dropped_clones = (int64_t)c[C_DROPPED];
     out->nb_overflow = (int64_t)c[C_NBOVF];
     out->bond_cap_overflow = (int64_t)c[C_CAPOVF];
+    out->nb_spilled = (int64_t)c[C_SPILLED];
     out->triplets = (int64_t)c[C_TRIPLETS];
     out->atom_updates = (int64_t)c[C_MOVED];
     for (int k = 0; k < REED_NPHASE; ++k) out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
@@ -1167,7 +1185,7 @@ void reed_destroy(reed_ctx* ctx)
     void* ptrs[] = {ctx->d_dsnap, ctx->d_pool, ctx->d_pool_state, ctx->d_hist, ctx->d_counters, ctx->d_splits, ctx->d_wsum, ctx->d_next, ctx->d_status, ctx->d_records,
                     ctx->d_rec_count, ctx->d_trace, ctx->d_trace_anchor, ctx->d_stacks, ctx->d_scratch,
                     ctx->d_thr, ctx->d_thr_hist, ctx->d_finished, ctx->d_damage, ctx->d_grads,
-                    ctx->d_adj, ctx->d_kde};
+                    ctx->d_adj, ctx->d_kde, ctx->d_spill};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1333,32 +1351,39 @@ int reed_forces(reed_ctx* ctx, int precision, double ion_Z, double ion_M, const 
     for (int i = 0; i < n; ++i)
         if (sp[i] < 0 || sp[i] >= ctx->nspec) return fail(ctx, REED_E_ARG, "species %d out of range", sp[i]);
     const bool f64 = precision == REED_PREC_FP64;
-    if (P.tt == REED_TT_TERSOFF) P.bond_cap = std::max(n, 1);   // every given atom is integrated
-    size_t smem = f64 ? reed_f64::smem_bytes(P.tt, P.na, P.bond_cap, 0, P.g_nbins)
-                      : reed_f32::smem_bytes(P.tt, P.na, P.bond_cap, 0, P.g_nbins);
+    // every given atom is integrated
+    if (P.tt == REED_TT_TERSOFF) P.bond_cap = std::max(n, 1);
+    P.act_cap = std::max(n, 1);
+    size_t smem = f64 ? reed_f64::smem_bytes(P.tt, P.na, P.bond_cap, 0, P.g_nbins, P.act_cap)
+                      : reed_f32::smem_bytes(P.tt, P.na, P.bond_cap, 0, P.g_nbins, P.act_cap);
     if (smem > ctx->smem_optin) return fail(ctx, REED_E_SMEM, "window needs %zu B shared memory", smem);
     size_t bx = up16(sizeof(double) * 3 * (size_t)std::max(n, 1)), bs = up16(sizeof(int) * (size_t)std::max(n, 1));
-    size_t bi = up16(sizeof(double) * 3), bo = up16(sizeof(double) * (5 + 3 * (size_t)std::max(n, 1)));
+    size_t bi = up16(sizeof(double) * 3), bo = up16(sizeof(double) * (6 + 3 * (size_t)std::max(n, 1)));
+    size_t bsp = up16(f64 ? reed_f64::spill_bytes(P.tt) : reed_f32::spill_bytes(P.tt));
     void* s = nullptr;
     int rc;
-    if ((rc = scratch(ctx, bx + bs + bi + bo, &s))) return rc;
+    if ((rc = scratch(ctx, bx + bs + bi + bo + bsp, &s))) return rc;
     double* dx = (double*)s;
     int* dsp = (int*)((char*)s + bx);
     double* dion = (double*)((char*)s + bx + bs);
     double* dout = (double*)((char*)s + bx + bs + bi);
+    unsigned char* dspill = bsp ? (unsigned char*)s + bx + bs + bi + bo : nullptr;
     if (n > 0) {
         CK(cudaMemcpy(dx, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(dsp, sp, sizeof(int) * n, cudaMemcpyHostToDevice));
     }
     CK(cudaMemcpy(dion, ion_x, sizeof(double) * 3, cudaMemcpyHostToDevice));
-    CK(f64 ? reed_f64::launch_forces(P.tt, P, n, dx, dsp, dion, dout, smem, 0)
-           : reed_f32::launch_forces(P.tt, P, n, dx, dsp, dion, dout, smem, 0));
-    std::vector<double> h(5 + 3 * (size_t)n);
+    CK(f64 ? reed_f64::launch_forces(P.tt, P, n, dx, dsp, dion, dout, dspill, smem, 0)
+           : reed_f32::launch_forces(P.tt, P, n, dx, dsp, dion, dout, dspill, smem, 0));
+    std::vector<double> h(6 + 3 * (size_t)n);
     CK(cudaMemcpy(h.data(), dout, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
     for (int d = 0; d < 3; ++d) f_ion[d] = h[d];
     if (energy) *energy = h[3];
     if (rho) *rho = h[4];
     for (int i = 0; i < 3 * n; ++i) f_atoms[i] = h[5 + i];
+    if (h[5 + 3 * (size_t)n] != 0.0)
+        return fail(ctx, REED_E_NEIGHBOR, "%.0f neighbour-list entries did not fit: forces incomplete",
+                    h[5 + 3 * (size_t)n]);
     return REED_OK;
 }
 
@@ -1406,12 +1431,14 @@ int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double*
 // reed_run_static: a run that allocates no device memory.
 //
 // The scratch of the stepper launch -- work counters, the primary queue head,
-// the status word and the per-CTA clone stacks -- lives in the file-scope
-// array below instead of context buffers.  It is part of this module's
-// image: every GPU that loads the library holds it until the process exits.
-// Host code must not pass the array's name to a kernel (on the host it is
-// only a stand-in for the device copy); the device address is obtained once
-// per device with cudaGetSymbolAddress and cached.
+// the status word, the per-CTA clone stacks and neighbour-list overflow rows
+// -- lives in the file-scope array below instead of context buffers.  It is
+// part of this module's image: every GPU that loads the library holds it
+// until the process exits.  Host code must not pass the array's name to a
+// kernel (on the host it is only a stand-in for the device copy); its device
+// address belongs to one CUDA context, so it is looked up with
+// cudaGetSymbolAddress once per device and context (set-up on the first call
+// there) and cached under the context's unique id.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
@@ -1423,10 +1450,44 @@ static __device__ __align__(256) unsigned char g_reed_static_scratch[REED_STATIC
 
 namespace {
 std::mutex g_static_mutex;
-void* g_static_addr[REED_STATIC_MAX_DEVICES] = {nullptr};
+struct StaticSlot {
+    unsigned long long ctx_id;   // unique id of the context the address belongs to (0: none yet)
+    void* addr;
+};
+StaticSlot g_static[REED_STATIC_MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device (set-up on the
-// first call for that device).
+// driver entry points, resolved through the runtime (no link against the driver library)
+typedef int (*CtxGetCurrentFn)(void** ctx);                          // cuCtxGetCurrent
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);         // cuCtxGetId
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+std::once_flag g_ctx_once;
+
+// Unique id of the calling thread's current context (0 if none is current).
+int current_context_id(unsigned long long* id)
+{
+    reed_ctx* ctx = nullptr;
+    std::call_once(g_ctx_once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = (CtxGetIdFn)f;
+    });
+    if (!g_ctx_current || !g_ctx_id) return fail(ctx, REED_E_CUDA, "reed_run_static: driver context queries unavailable");
+    void* c = nullptr;
+    if (g_ctx_current(&c) != 0) return fail(ctx, REED_E_CUDA, "reed_run_static: cuCtxGetCurrent failed");
+    *id = 0;
+    if (c && g_ctx_id(c, id) != 0) return fail(ctx, REED_E_CUDA, "reed_run_static: cuCtxGetId failed");
+    return REED_OK;
+}
+
+// Device address of the scratch array in the current device's current
+// context: looked up on the first call in that context, then cached.
 int static_scratch(void** out)
 {
     reed_ctx* ctx = nullptr;
@@ -1434,13 +1495,19 @@ int static_scratch(void** out)
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= REED_STATIC_MAX_DEVICES)
         return fail(nullptr, REED_E_ARG, "reed_run_static: device %d out of range", dev);
+    unsigned long long id = 0;
+    int rc = current_context_id(&id);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_addr[dev]) {
+    StaticSlot& slot = g_static[dev];
+    if (id == 0 || slot.ctx_id != id || !slot.addr) {
         void* p = nullptr;
-        CK(cudaGetSymbolAddress(&p, g_reed_static_scratch));
-        g_static_addr[dev] = p;
+        CK(cudaGetSymbolAddress(&p, g_reed_static_scratch));   // makes the runtime's context current if none was
+        if (id == 0 && (rc = current_context_id(&id))) return rc;
+        slot.addr = p;
+        slot.ctx_id = id;
     }
-    *out = g_static_addr[dev];
+    *out = slot.addr;
     return REED_OK;
 }
 }  // namespace
@@ -1486,7 +1553,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     if (const char* m = beam_error(*lat, o)) return fail(nullptr, REED_E_ARG, "%s", m);
     if (o.precision != REED_PREC_MIXED && o.precision != REED_PREC_FP64) return fail(nullptr, REED_E_ARG, "precision");
     if (o.threads_per_track && !valid_threads(o.threads_per_track))
-        return fail(nullptr, REED_E_ARG, "threads_per_track must be 0, 32, 64, 128 or 256");
+        return fail(nullptr, REED_E_ARG, "threads_per_track must be 0, 32, 64, 128, 256 or 512");
     if (o.ctas_per_sm < 0) return fail(nullptr, REED_E_ARG, "negative ctas_per_sm");
     if (o.record_tracks || o.trace_tracks || o.trace_steps)
         return fail(nullptr, REED_E_ARG, "reed_run_static keeps no per-track records or traces");
@@ -1517,8 +1584,8 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
 
     const int tt = P.tt;
     const bool f64 = o.precision == REED_PREC_FP64;
-    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap, 0, P.g_nbins)
-                            : reed_f32::smem_bytes(tt, P.na, P.bond_cap, 0, P.g_nbins);
+    const size_t smem = f64 ? reed_f64::smem_bytes(tt, P.na, P.bond_cap, 0, P.g_nbins, P.act_cap)
+                            : reed_f32::smem_bytes(tt, P.na, P.bond_cap, 0, P.g_nbins, P.act_cap);
     if (smem > (size_t)optin)
         return fail(nullptr, REED_E_SMEM, "window of %d atoms needs %zu B of shared memory (max %d)", P.na, smem, optin);
     LaunchCfg L;
@@ -1530,20 +1597,22 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     if (occ < 1) return fail(nullptr, REED_E_SMEM, "kernel does not fit on an SM");
     L.ctas_per_sm = o.ctas_per_sm ? std::min(o.ctas_per_sm, occ) : occ;
 
-    // clone stacks must fit in the static scratch: fewer CTAs per SM if needed
+    // clone stacks and overflow rows must fit in the static scratch: fewer
+    // CTAs per SM if needed
     DevBuf B;
     std::memset(&B, 0, sizeof(B));
     B.entry_bytes = f64 ? reed_f64::entry_bytes(tt, P.na) : reed_f32::entry_bytes(tt, P.na);
     B.stack_depth = P.nthr;
-    B.stack_stride = B.entry_bytes * (size_t)std::max(P.nthr, 1);
+    B.stack_stride = P.nthr > 0 ? B.entry_bytes * (size_t)P.nthr : 0;
+    B.spill_stride = f64 ? reed_f64::spill_bytes(tt) : reed_f32::spill_bytes(tt);
     const size_t room = REED_STATIC_SCRATCH_BYTES - REED_STATIC_HEADER;
-    if (P.nthr > 0) {
-        while (L.ctas_per_sm > 1 && B.stack_stride * (size_t)desc.sms * L.ctas_per_sm > room) --L.ctas_per_sm;
-        if (B.stack_stride * (size_t)desc.sms * L.ctas_per_sm > room)
-            return fail(nullptr, REED_E_ARG,
-                        "clone stacks need %zu B (%d SMs x %d levels x %zu B), more than the %zu B static scratch",
-                        B.stack_stride * (size_t)desc.sms, desc.sms, P.nthr, B.entry_bytes, room);
-    }
+    const size_t per_cta = B.stack_stride + B.spill_stride;
+    while (L.ctas_per_sm > 1 && per_cta * (size_t)desc.sms * L.ctas_per_sm > room) --L.ctas_per_sm;
+    if (per_cta * (size_t)desc.sms * L.ctas_per_sm > room)
+        return fail(nullptr, REED_E_ARG,
+                    "clone stacks and list overflow rows need %zu B (%d SMs x (%d levels x %zu B + %zu B)), more "
+                    "than the %zu B static scratch",
+                    per_cta * (size_t)desc.sms, desc.sms, P.nthr, B.entry_bytes, B.spill_stride, room);
     L.grid = desc.sms * L.ctas_per_sm;
 
     unsigned char* base = nullptr;
@@ -1560,6 +1629,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     B.damage = nullptr;
     P.stop_after = o.target_tracks;
     B.stacks = P.nthr > 0 ? base + REED_STATIC_HEADER : nullptr;
+    B.spill = B.spill_stride ? base + REED_STATIC_HEADER + B.stack_stride * (size_t)L.grid : nullptr;
     B.hist = hist_out;
     B.records = nullptr;
     B.trace = nullptr;
@@ -1590,6 +1660,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
         stats_out->dropped_clones = (int64_t)c[C_DROPPED];
         stats_out->nb_overflow = (int64_t)c[C_NBOVF];
         stats_out->bond_cap_overflow = (int64_t)c[C_CAPOVF];
+        stats_out->nb_spilled = (int64_t)c[C_SPILLED];
         stats_out->failed = (int64_t)c[C_FAILED];
         stats_out->stopped = (int64_t)c[C_STOP];
         stats_out->backscattered = (int64_t)c[C_BACK];
@@ -1611,9 +1682,9 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
     }
     if (status & ERR_NONFINITE) return fail(nullptr, REED_E_NONFINITE, "a track became non-finite");
     if (status & ERR_QUEUE) return fail(nullptr, REED_E_QUEUE_FULL, "clone stack overflow: clones dropped");
-    if (status & ERR_NEIGHBOR) {
-        fail(nullptr, REED_W_NEIGHBOR, "neighbour lists truncated (see nb_overflow)");
-        return REED_W_NEIGHBOR;
-    }
+    if (status & ERR_NEIGHBOR)
+        return fail(nullptr, REED_E_NEIGHBOR,
+                    "a neighbour list outgrew its overflow row or the overflow rows ran out (see nb_overflow): "
+                    "forces were incomplete");
     return REED_OK;
 }

@@ -18,25 +18,37 @@
 #define REED_MAX_BASIS 12
 #define REED_MAX_THR 16
 #define REED_MAX_WARPS 16
-#define REED_MAXNB 12           // Tersoff neighbours kept per atom
-#define REED_MAXNB_PAIR 64      // pair-potential neighbours kept per atom
+#define REED_MAXNB 12           // Tersoff neighbours per atom held in shared memory
+#define REED_MAXNB_PAIR 64      // pair-potential neighbours per atom held in shared memory
+#define REED_FAST_NB 4          // Tersoff atoms with at most this many list neighbours take the unrolled path
+#define REED_BF_STRIDE 13       // row stride of the per-bond force rows (odd: lanes hit distinct banks)
+// An atom with more list neighbours than its shared-memory row holds keeps
+// its whole list in an overflow row in global memory (per CTA, rebuilt with
+// the lists); only beyond these limits is a run refused (REED_E_NEIGHBOR).
+#define REED_SPILL_ROWS 32      // overflow rows per CTA
+#define REED_SPILL_TERSOFF 64   // entries of a Tersoff overflow row
+#define REED_SPILL_PAIR 192     // entries of a pair-list overflow row
 
-// neighbour-list capacity per atom for a target model
+// neighbour-list capacity per atom in shared memory, and of an overflow row
 __host__ __device__ constexpr int maxnb(int tt) { return tt == REED_TT_BUCKINGHAM ? REED_MAXNB_PAIR : REED_MAXNB; }
+__host__ __device__ constexpr int spill_width(int tt)
+{
+    return tt == REED_TT_BUCKINGHAM ? REED_SPILL_PAIR : (tt == REED_TT_TERSOFF ? REED_SPILL_TERSOFF : 0);
+}
 
 // slot flags carried in pos.w (exact small integers in either precision):
 //   w = species (0/1) for an integrated atom, species + 2 for a frozen atom,
 //   -1 for an empty slot (cell above the surface).
 #define REED_W_EMPTY (-1)
 
-enum { REED_NCOUNT = 24 };
+enum { REED_NCOUNT = 25 };
 enum { REED_NRED = 9 };   // per-warp partial sums of a force pass
 // cycle counters of the step phases (thread 0 of every CTA, summed)
 enum { PH_ION = 0, PH_MOVE, PH_BUILD, PH_PASS1, PH_FORCE, PH_ADMIN, REED_NPHASE };
 #define C_PHASE0 C_SPARE
 enum {
     C_PRIMARIES = 0, C_CLONES, C_TRACKS, C_STEPS, C_PAIRS, C_BONDS, C_SHIFTS, C_REBUILDS,
-    C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_CAPOVF, C_TRIPLETS, C_MOVED, C_SPARE
+    C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_CAPOVF, C_TRIPLETS, C_MOVED, C_SPILLED, C_SPARE
 };   // C_SPARE .. C_SPARE + REED_NPHASE - 1 hold the phase clocks
 enum { W_STOPPED = 0, W_BACK, W_TRUNC, W_FAILED };
 
@@ -91,7 +103,8 @@ struct DevParams {
     double bA[3], brho_inv[3], bC[3];
     double b_rt, b_rc, b_lo, b_hi;
     double b_zk[3], b_zia[3];
-    int bond_cap;                      // Tersoff bond-storage rows (needed atoms)
+    int bond_cap;                      // neighbour-list rows (Tersoff: needed atoms)
+    int act_cap;                       // integrated atoms a window can hold (rows of the per-bond forces)
     // electronic stopping (Sec. 2 "Third")
     double gamma, s_loc, rho0_inv, lam_inv;
     int rho_on;
@@ -151,6 +164,8 @@ struct DevBuf {
     size_t adj_stride;
     double* grads;                  // 8 per track record: dz/dtheta
     unsigned long long* finished;   // tracks finished in this run (stop rule)
+    unsigned char* spill;           // per-CTA neighbour-list overflow rows (target models), or null
+    size_t spill_stride;
 };
 
 enum { ERR_QUEUE = 1, ERR_NONFINITE = 2, ERR_NEIGHBOR = 4, ERR_TIMEOUT = 8 };

@@ -123,13 +123,11 @@ template <typename R> __device__ __forceinline__ R ters_b(const HotParams<R>& H,
     return b;
 }
 
-// V_ab at fixed bond order b: value V, radial derivative dV, and
-// pre_fA = (1 - s) fc fA (the coefficient of b in V_ab).
+// V_ab at fixed bond order b, given fc(r) and its derivative: value V,
+// radial derivative dV, and pre_fA = (1 - s) fc fA (the coefficient of b in V_ab).
 template <typename R>
-__device__ __forceinline__ void ters_pair(const HotParams<R>& H, R r, R b, R& V, R& dV, R& pre_fA)
+__device__ __forceinline__ void ters_pair(const HotParams<R>& H, R r, R fc, R dfc, R b, R& V, R& dV, R& pre_fA)
 {
-    R dfc;
-    const R fc = ters_fc<R>(H, r, dfc);
     const R fR = H.tA * Mth<R>::exp(-H.tl1 * r);
     const R fA = -H.tB * Mth<R>::exp(-H.tl2 * r);
     const R VT = fc * (fR + b * fA);

@@ -68,6 +68,8 @@ template <typename R> struct TrackShared {
     int Aold[3];
     int shift, event, status, src, top, nclone, slot;
     int need_count, active_count;
+    int nspill;           // overflow rows taken by the current lists
+    int nfast;            // Tersoff: slots of the unrolled path (the first nfast of `order`)
     int scan[2][REED_MAX_WARPS];
     long long pidx;
     R red[REED_MAX_WARPS][REED_NRED];
@@ -77,11 +79,15 @@ template <typename R> struct TrackShared {
 template <typename R> struct V2 { R a, b; };
 
 // Shared-memory carve-up for a window of na atoms.  Target neighbour lists
-// and Tersoff bond data are kept only for "needed" atoms -- integrated atoms
-// (slots 0 .. active_count-1) and atoms bonded to them -- at most cap of
-// them, addressed through need_map (atom -> slot) and slot_atom.  The
+// are kept only for "needed" atoms -- integrated atoms (slots 0 ..
+// active_count-1) and, for Tersoff, the atoms bonded to them -- at most cap
+// of them, addressed through need_map (atom -> slot) and slot_atom.  The
 // neighbour search bins atoms on a grid of nbins cells (bin_count is all
-// zero between builds).
+// zero between builds).  Tersoff adds, per list entry, the position of the
+// centre in the neighbour's own list (rev), the order in which the centre
+// pass visits the slots, and for each integrated atom (at most act of them)
+// one force row: entry q holds the force that the bonds centred on its q-th
+// neighbour exert on it.
 
 template <typename R, int TT> struct Layout {
     static __host__ __device__ size_t align(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -98,21 +104,36 @@ template <typename R, int TT> struct Layout {
                align(cap) +                              // nnb
                align(sizeof(uint16_t) * cap * maxnb(TT));     // nbr
     }
-    static __host__ __device__ size_t bond_bytes(int cap)
+    static __host__ __device__ size_t bond_bytes(int cap, int act)
     {
-        return TT == REED_TT_TERSOFF ? align(sizeof(V2<R>) * cap * REED_MAXNB) : 0;
+        if (TT != REED_TT_TERSOFF) return 0;
+        return align((size_t)cap * REED_MAXNB) +                       // rev
+               align(sizeof(uint16_t) * cap) +                         // order
+               3 * align(sizeof(R) * (size_t)act * REED_BF_STRIDE);    // per-bond forces (x, y, z)
     }
     static __host__ __device__ size_t adj_bytes(int na, int adj) { return adj ? 2 * align(sizeof(V4<R>) * na) : 0; }
-    static __host__ __device__ size_t total(int na, int cap, int adj = 0, int nbins = 0)
+    static __host__ __device__ size_t total(int na, int cap, int adj = 0, int nbins = 0, int act = 0)
     {
-        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap, nbins) + bond_bytes(cap) + adj_bytes(na, adj);
+        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap, nbins) + bond_bytes(cap, act) +
+               adj_bytes(na, adj);
     }
     // bytes of one clone record: ion header + pos, vel, frc
     static __host__ __device__ size_t entry_bytes(int na) { return align(sizeof(IonState<R>)) + atoms_bytes(na); }
+    // per-CTA overflow rows in global memory: neighbours (and, for Tersoff,
+    // the reverse entries and the per-bond forces of an integrated atom)
+    static __host__ __device__ size_t spill_bytes()
+    {
+        constexpr size_t W = (size_t)spill_width(TT), N = REED_SPILL_ROWS;
+        if (TT == REED_TT_NONE) return 0;
+        size_t b = align(sizeof(uint16_t) * N * W);
+        if (TT == REED_TT_TERSOFF) b += align(N * W) + align(sizeof(R) * 3 * N * W);
+        return b;
+    }
 };
 
 #define REED_NO_SLOT 0xFFFFu
 #define REED_PENDING 0xFFFEu
+#define REED_NO_REV 0xFFu
 
 template <typename R, int TT> struct Win {
     TrackShared<R>* S;
@@ -126,21 +147,31 @@ template <typename R, int TT> struct Win {
     uint16_t* slot_atom;  // list slot -> atom
     uint8_t* nnb;         // neighbours per slot
     uint16_t* nbr;        // neighbour atoms per slot
-    V2<R>* bond;          // per slot and neighbour: {1/2 dV/db db/dzeta, dV/dr}
+    uint8_t* rev;         // Tersoff: per slot and neighbour, the centre's entry in the neighbour's list
+    uint16_t* order;      // Tersoff: slots in the order the centre pass takes them
+    R* bfx;               // Tersoff: per integrated slot and list entry, the force of the
+    R* bfy;               //   bonds centred on that neighbour (row stride REED_BF_STRIDE)
+    R* bfz;
+    uint16_t* sp_nbr;     // overflow rows in global memory (may be null)
+    uint8_t* sp_rev;
+    R* sp_bf;             // x, y, z blocks of REED_SPILL_TERSOFF per row
     V4<R>* xbar;          // adjoint of positions (adjoint runs)
     V4<R>* vbar;          // adjoint of velocities
     // Neighbour q of list slot k is nbr[k * nb_slot + q * nb_q]: slot-major for
     // Tersoff (a thread walks its own short list), neighbour-major for the
     // 64-entry pair lists (consecutive slots, i.e. lanes, hit consecutive words).
-    int nb_slot, nb_q;
+    // A slot with more neighbours than the shared row holds keeps its whole
+    // list in an overflow row; entry 0 of the shared row is then that row's index.
+    int nb_slot, nb_q, act_cap;
     // zero the bin counters (all threads; a barrier must follow)
     __device__ void clear_grid(const DevParams& P)
     {
         if (bin_count)
             for (int b = threadIdx.x; b < P.g_nbins; b += blockDim.x) bin_count[b] = 0u;
     }
-    __device__ Win(unsigned char* base, int na, int cap, int adj = 0, int nbins = 0)
-        : nb_slot(TT == REED_TT_BUCKINGHAM ? 1 : maxnb(TT)), nb_q(TT == REED_TT_BUCKINGHAM ? cap : 1)
+    __device__ Win(unsigned char* base, int na, int cap, int adj = 0, int nbins = 0, int act = 0,
+                   unsigned char* spill = nullptr)
+        : nb_slot(TT == REED_TT_BUCKINGHAM ? 1 : maxnb(TT)), nb_q(TT == REED_TT_BUCKINGHAM ? cap : 1), act_cap(act)
     {
         using L = Layout<R, TT>;
         S = reinterpret_cast<TrackShared<R>*>(base);
@@ -157,7 +188,12 @@ template <typename R, int TT> struct Win {
         slot_atom = nullptr;
         nnb = nullptr;
         nbr = nullptr;
-        bond = nullptr;
+        rev = nullptr;
+        order = nullptr;
+        bfx = bfy = bfz = nullptr;
+        sp_nbr = nullptr;
+        sp_rev = nullptr;
+        sp_bf = nullptr;
         if constexpr (TT != REED_TT_NONE) {
             need_map = reinterpret_cast<uint16_t*>(base + o);
             o += L::align(sizeof(uint16_t) * na);
@@ -173,15 +209,52 @@ template <typename R, int TT> struct Win {
             o += L::align(cap);
             nbr = reinterpret_cast<uint16_t*>(base + o);
             o += L::align(sizeof(uint16_t) * cap * maxnb(TT));
+            if (spill) sp_nbr = reinterpret_cast<uint16_t*>(spill);
         }
         if constexpr (TT == REED_TT_TERSOFF) {
-            bond = reinterpret_cast<V2<R>*>(base + o);
-            o += L::bond_bytes(cap);
+            rev = base + o;
+            o += L::align((size_t)cap * REED_MAXNB);
+            order = reinterpret_cast<uint16_t*>(base + o);
+            o += L::align(sizeof(uint16_t) * cap);
+            const size_t fb = L::align(sizeof(R) * (size_t)act * REED_BF_STRIDE);
+            bfx = reinterpret_cast<R*>(base + o);
+            bfy = reinterpret_cast<R*>(base + o + fb);
+            bfz = reinterpret_cast<R*>(base + o + 2 * fb);
+            o += 3 * fb;
+            if (spill) {
+                constexpr size_t W = REED_SPILL_TERSOFF, N = REED_SPILL_ROWS;
+                sp_rev = spill + L::align(sizeof(uint16_t) * N * W);
+                sp_bf = reinterpret_cast<R*>(spill + L::align(sizeof(uint16_t) * N * W) + L::align(N * W));
+            }
         }
         xbar = vbar = nullptr;
         if (adj) {
             xbar = reinterpret_cast<V4<R>*>(base + o);
             vbar = reinterpret_cast<V4<R>*>(base + o + L::align(sizeof(V4<R>) * na));
+        }
+    }
+    // list of slot k with m entries: its shared row, or its overflow row
+    __device__ __forceinline__ const uint16_t* list(int k, int m) const
+    {
+        return m <= maxnb(TT) ? nbr + (size_t)k * nb_slot : sp_nbr + (size_t)nbr[(size_t)k * nb_slot] * spill_width(TT);
+    }
+    __device__ __forceinline__ uint8_t* rev_row(int k, int m) const
+    {
+        return m <= REED_MAXNB ? rev + (size_t)k * REED_MAXNB : sp_rev + (size_t)nbr[(size_t)k * REED_MAXNB] * REED_SPILL_TERSOFF;
+    }
+    // force of the bonds centred on entry e's atom on the integrated atom of slot s
+    __device__ __forceinline__ void bf_store(int s, int e, R fx, R fy, R fz) const
+    {
+        if (nnb[s] <= REED_MAXNB) {
+            const int o = s * REED_BF_STRIDE + e;
+            bfx[o] = fx;
+            bfy[o] = fy;
+            bfz[o] = fz;
+        } else {
+            R* b = sp_bf + (size_t)nbr[(size_t)s * REED_MAXNB] * 3 * REED_SPILL_TERSOFF;
+            b[e] = fx;
+            b[REED_SPILL_TERSOFF + e] = fy;
+            b[2 * REED_SPILL_TERSOFF + e] = fz;
         }
     }
 };
@@ -358,13 +431,20 @@ __device__ __forceinline__ int grid_bin(const DevParams& P, const HotParams<R>& 
     return (grid_axis<R>(P, H, p.x) * P.g_nb + grid_axis<R>(P, H, p.y)) * P.g_nb + grid_axis<R>(P, H, p.z);
 }
 
+// Neighbours of atom i within the list radius, in bin order, into list slot
+// `slot`.  Past the shared row's capacity the list moves to an overflow row
+// in global memory; past that row's capacity (or with no row left) the
+// entries are dropped and counted in `overflow`, which fails the run.
 template <typename R, int TT>
 __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int i, int slot,
                                       int& overflow)
 {
+    constexpr int NS = maxnb(TT), NW = spill_width(TT);
     const V4<R> pi = W.pos[i];
     uint16_t* out = W.nbr + (size_t)slot * W.nb_slot;
     const int oq = W.nb_q;
+    uint16_t* sp = nullptr;   // overflow row, once the shared row is full
+    bool asked = false;
     int cnt = 0;
     const int nb = P.g_nb;
     const int bx = grid_axis<R>(P, H, pi.x), by = grid_axis<R>(P, H, pi.y), bz = grid_axis<R>(P, H, pi.z);
@@ -380,8 +460,26 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
                 const V4<R> pj = W.pos[j];
                 const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                 if (dx * dx + dy * dy + dz * dz < H.rlist2) {
-                    if (cnt < maxnb(TT)) out[(size_t)(cnt++) * oq] = (uint16_t)j;
-                    else ++overflow;
+                    if (cnt < NS) {
+                        out[(size_t)cnt * oq] = (uint16_t)j;
+                        ++cnt;
+                    } else {
+                        if (!asked && W.sp_nbr) {
+                            asked = true;
+                            const int r = atomicAdd(&W.S->nspill, 1);
+                            if (r < REED_SPILL_ROWS) {
+                                sp = W.sp_nbr + (size_t)r * NW;
+                                for (int e = 0; e < NS; ++e) sp[e] = out[(size_t)e * oq];
+                                out[0] = (uint16_t)r;
+                            }
+                        }
+                        if (sp && cnt < NW) {
+                            sp[cnt] = (uint16_t)j;
+                            ++cnt;
+                        } else {
+                            ++overflow;
+                        }
+                    }
                     if (TT == REED_TT_TERSOFF && !is_active(pj) && W.need_map[j] == REED_NO_SLOT)
                         W.need_map[j] = (uint16_t)REED_PENDING;
                 }
@@ -430,7 +528,7 @@ __device__ __forceinline__ void block_scan2(TrackShared<R>* S, int c0, int c1, i
 
 template <typename R, int TT>
 __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow,
-                                 int& cap_overflow)
+                                 int& cap_overflow, unsigned long long& spilled)
 {
     const int na = P.na, nbins = P.g_nbins;
     TrackShared<R>* S = W.S;
@@ -438,6 +536,7 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
     const int i0 = min(na, (int)threadIdx.x * chunk), i1 = min(na, i0 + chunk);
     const int bchunk = (nbins + blockDim.x - 1) / blockDim.x;
     const int j0 = min(nbins, (int)threadIdx.x * bchunk), j1 = min(nbins, j0 + bchunk);
+    if (threadIdx.x == 0) S->nspill = 0;
     // bin populations and integrated atoms of this thread's chunk
     int nact = 0;
     for (int i = i0; i < i1; ++i) {
@@ -503,7 +602,10 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
     __syncthreads();
     if constexpr (TT != REED_TT_TERSOFF) {
         // pair potentials need lists of the integrated atoms only
-        if (threadIdx.x == 0) S->need_count = nact_slots;
+        if (threadIdx.x == 0) {
+            S->need_count = nact_slots;
+            spilled += (unsigned long long)min(S->nspill, REED_SPILL_ROWS);
+        }
         __syncthreads();
         return;
     }
@@ -531,156 +633,346 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
         W.nnb[k] = (uint8_t)list_of<R, TT>(P, H, W, i, k, overflow);
     }
     __syncthreads();
-    if (threadIdx.x == 0) S->need_count = nneed;
+    if (threadIdx.x == 0) {
+        S->need_count = nneed;
+        spilled += (unsigned long long)min(S->nspill, REED_SPILL_ROWS);
+    }
     // (pending marks set by these last lists are not needed: clear them)
     for (int i = threadIdx.x; i < na; i += blockDim.x)
         if (W.need_map[i] == REED_PENDING) W.need_map[i] = (uint16_t)REED_NO_SLOT;
     __syncthreads();
-}
-
-// Tersoff pass 1 for the atom in list slot k: for each bond (a, b) store
-// {pre_ab = 1/2 dV_ab/db * db/dzeta_ab, dV_ab/dr}; returns 1/2 sum_b V_ab.
-// For an integrated atom (k < active_count) it also writes to frc[a] the
-// part of the force on a that its own bonds give: the radial terms
-// 1/2 dV_ab/dr and a as the centre of every zeta_ab (the derivative of zeta
-// with respect to x_a is summed alongside zeta itself).
-template <typename R, int TT>
-__device__ R ters_pass1(const HotParams<R>& H, Win<R, TT>& W, int k, unsigned long long& triplets)
-{
-    const int a = W.slot_atom[k];
-    const int m = W.nnb[k];
-    const bool own = k < W.S->active_count;
-    const uint16_t* nb = W.nbr + (size_t)k * REED_MAXNB;
-    V2<R>* bond = W.bond + (size_t)k * REED_MAXNB;
-    const V4<R> pa = W.pos[a];
-    R E = R(0);
-    R fx = R(0), fy = R(0), fz = R(0);
-    for (int q = 0; q < m; ++q) {
-        const V4<R> pq = W.pos[nb[q]];
-        const R qx = pq.x - pa.x, qy = pq.y - pa.y, qz = pq.z - pa.z;
-        const R r2q = qx * qx + qy * qy + qz * qz;
-        const R irq = Mth<R>::rsqrt(r2q);
-        const R rq = r2q * irq;
-        const R ux = qx * irq, uy = qy * irq, uz = qz * irq;   // unit a -> q
-        R zeta = R(0);
-        R dx = R(0), dy = R(0), dz = R(0);   // d zeta / d x_a
-        for (int p = 0; p < m; ++p) {
-            if (p == q) continue;
-            const V4<R> pk = W.pos[nb[p]];
-            const R kx = pk.x - pa.x, ky = pk.y - pa.y, kz = pk.z - pa.z;
-            const R r2k = kx * kx + ky * ky + kz * kz;
-            const R irk = Mth<R>::rsqrt(r2k);
-            R dfc;
-            const R fck = ters_fc<R>(H, r2k * irk, dfc);
-            if (fck <= R(0) && dfc == R(0)) continue;
-            const R vx = kx * irk, vy = ky * irk, vz = kz * irk;   // unit a -> p
-            const R c = ux * vx + uy * vy + uz * vz;
-            R dg;
-            const R g = ters_g<R>(H, c, dg);
-            zeta += fck * g;
-            ++triplets;
-            if (own) {
-                // d c / d x_a = -[(v - c u)/r_q + (u - c v)/r_p]
-                const R cx = (vx - c * ux) * irq + (ux - c * vx) * irk;
-                const R cy = (vy - c * uy) * irq + (uy - c * vy) * irk;
-                const R cz = (vz - c * uz) * irq + (uz - c * vz) * irk;
-                const R t = fck * dg;
-                dx += -dfc * g * vx - t * cx;
-                dy += -dfc * g * vy - t * cy;
-                dz += -dfc * g * vz - t * cz;
+    // reverse entries: where the centre of slot k sits in the list of each
+    // integrated neighbour (lists are symmetric: the same distance test from
+    // both ends), so the centre pass can leave its force there
+    for (int k = threadIdx.x; k < nneed; k += blockDim.x) {
+        const int a = W.slot_atom[k], m = W.nnb[k];
+        const uint16_t* row = W.list(k, m);
+        uint8_t* rv = W.rev_row(k, m);
+        for (int q = 0; q < m; ++q) {
+            const unsigned sp = W.need_map[row[q]];
+            uint8_t e = (uint8_t)REED_NO_REV;
+            if (sp < (unsigned)nact_slots) {
+                const int mp = W.nnb[sp];
+                const uint16_t* prow = W.list((int)sp, mp);
+                for (int t = 0; t < mp; ++t)
+                    if (prow[t] == a) {
+                        e = (uint8_t)t;
+                        break;
+                    }
+                if (e == (uint8_t)REED_NO_REV) ++overflow;   // only with a truncated list
             }
-        }
-        R db;
-        const R b = ters_b<R>(H, zeta, db);
-        R V, dV, pfa;
-        ters_pair<R>(H, rq, b, V, dV, pfa);
-        V2<R> o;
-        o.a = R(0.5) * pfa * db;
-        o.b = dV;
-        bond[q] = o;
-        E += R(0.5) * V;
-        if (own) {
-            fx += R(0.5) * dV * ux - o.a * dx;
-            fy += R(0.5) * dV * uy - o.a * dy;
-            fz += R(0.5) * dV * uz - o.a * dz;
+            rv[q] = e;
         }
     }
-    if (own) {
+    // the centre pass takes slots with at most REED_FAST_NB neighbours first
+    // (one thread each, unrolled), then the rest (one warp each)
+    {
+        const int kc = (nneed + blockDim.x - 1) / blockDim.x;
+        const int k0 = min(nneed, (int)threadIdx.x * kc), k1 = min(nneed, k0 + kc);
+        int nf = 0;
+        for (int k = k0; k < k1; ++k) nf += W.nnb[k] <= REED_FAST_NB;
+        int of, os, tf, ts;
+        block_scan2<R>(S, nf, (k1 - k0) - nf, of, os, tf, ts);
+        os += tf;
+        for (int k = k0; k < k1; ++k) W.order[W.nnb[k] <= REED_FAST_NB ? of++ : os++] = (uint16_t)k;
+        if (threadIdx.x == 0) S->nfast = tf;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Tersoff forces, one centre at a time.  The energy of the bonds centred on
+// atom a,
+//     E_a = 1/2 sum_j V(r_j, b_j),   b_j = b(zeta_j),
+//     zeta_j = sum_{k != j} fc(r_k) g(c_jk),   c_jk = u_j . u_k,
+// (j, k over a's neighbours, u_j the unit vector from a to j) depends on the
+// positions of a and its neighbours only.  With P_j = 1/2 dV_j/db db_j/dzeta
+// and Q_j = 1/2 dV_j/dr, the force it exerts on neighbour p is
+//     F_p = -u_p [Q_p + fc'(r_p) sum_{j != p} P_j g(c_jp)]
+//           - (1 / r_p) sum_{j != p} [P_j fc(r_p) + P_p fc(r_j)] g'(c_jp) (u_j - c_jp u_p)
+// and on a itself -sum_p F_p.  The centre pass evaluates every needed atom
+// once and leaves F_p in the force row of each integrated neighbour p (at
+// a's entry in p's list) and -sum_p F_p in frc[a] when a is integrated; the
+// force phase then sums each integrated atom's row in list order.  Every
+// term is written by one thread and summed in a fixed order, so results do
+// not depend on thread timing.
+// ---------------------------------------------------------------------------
+
+// Atoms with at most REED_FAST_NB neighbours: everything in registers
+// (unrolled; missing neighbours have fc = P = Q = 0 and contribute nothing).
+template <typename R, int TT>
+__device__ __forceinline__ R ters_centre_fast(const HotParams<R>& H, Win<R, TT>& W, int k, int m, int nact,
+                                              unsigned long long& triplets)
+{
+    constexpr int M = REED_FAST_NB;
+    const int a = W.slot_atom[k];
+    const V4<R> pa = W.pos[a];
+    const uint16_t* row = W.nbr + (size_t)k * REED_MAXNB;
+    const uint8_t* rv = W.rev + (size_t)k * REED_MAXNB;
+    R ux[M], uy[M], uz[M], ir[M], rr[M], fc[M], dfc[M];
+    int idx[M];
+    int npos = 0;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        ux[q] = uy[q] = uz[q] = ir[q] = rr[q] = fc[q] = dfc[q] = R(0);
+        idx[q] = -1;
+        if (q < m) {
+            idx[q] = row[q];
+            const V4<R> pq = W.pos[idx[q]];
+            const R dx = pq.x - pa.x, dy = pq.y - pa.y, dz = pq.z - pa.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            ir[q] = Mth<R>::rsqrt(r2);
+            rr[q] = r2 * ir[q];
+            ux[q] = dx * ir[q];
+            uy[q] = dy * ir[q];
+            uz[q] = dz * ir[q];
+            fc[q] = ters_fc<R>(H, rr[q], dfc[q]);
+            npos += (fc[q] > R(0) || dfc[q] != R(0)) ? 1 : 0;
+        }
+    }
+    if (m > 1) triplets += (unsigned long long)((m - 1) * npos);
+    // angle terms of every pair of neighbours
+    R c[M][M], g[M][M], dg[M][M];
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+#pragma unroll
+        for (int p = q + 1; p < M; ++p) {
+            c[q][p] = ux[q] * ux[p] + uy[q] * uy[p] + uz[q] * uz[p];
+            g[q][p] = ters_g<R>(H, c[q][p], dg[q][p]);
+        }
+    // bond orders, bond energies and their derivatives
+    R P[M], Q[M];
+    R E = R(0);
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        R zeta = R(0);
+#pragma unroll
+        for (int p = 0; p < M; ++p)
+            if (p != q) zeta += fc[p] * (p < q ? g[p][q] : g[q][p]);
+        P[q] = Q[q] = R(0);
+        if (q < m && (fc[q] > R(0) || dfc[q] != R(0))) {
+            R db, V, dV, pfa;
+            const R b = ters_b<R>(H, zeta, db);
+            ters_pair<R>(H, rr[q], fc[q], dfc[q], b, V, dV, pfa);
+            P[q] = R(0.5) * pfa * db;
+            Q[q] = R(0.5) * dV;
+            E += R(0.5) * V;
+        }
+    }
+    // forces on the neighbours
+    R fx[M], fy[M], fz[M];
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        R sg = R(0);
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            if (j != p) sg += P[j] * (j < p ? g[j][p] : g[p][j]);
+        const R A = Q[p] + dfc[p] * sg;
+        fx[p] = -A * ux[p];
+        fy[p] = -A * uy[p];
+        fz[p] = -A * uz[p];
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+#pragma unroll
+        for (int p = j + 1; p < M; ++p) {
+            const R w = (P[j] * fc[p] + P[p] * fc[j]) * dg[j][p];
+            const R wp = w * ir[p], wj = w * ir[j], cc = c[j][p];
+            fx[p] -= wp * (ux[j] - cc * ux[p]);
+            fy[p] -= wp * (uy[j] - cc * uy[p]);
+            fz[p] -= wp * (uz[j] - cc * uz[p]);
+            fx[j] -= wj * (ux[p] - cc * ux[j]);
+            fy[j] -= wj * (uy[p] - cc * uy[j]);
+            fz[j] -= wj * (uz[p] - cc * uz[j]);
+        }
+    R ax = R(0), ay = R(0), az = R(0);
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        ax -= fx[p];
+        ay -= fy[p];
+        az -= fz[p];
+        if (p < m) {
+            const unsigned s = W.need_map[idx[p]];
+            if (s < (unsigned)nact && rv[p] != (uint8_t)REED_NO_REV) W.bf_store((int)s, rv[p], fx[p], fy[p], fz[p]);
+        }
+    }
+    if (k < nact) {
         V4<R> f;
-        f.x = fx;
-        f.y = fy;
-        f.z = fz;
+        f.x = ax;
+        f.y = ay;
+        f.z = az;
         f.w = R(0);
         W.frc[a] = f;
     }
     return E;
 }
 
-// Tersoff pass 2: the rest of the force on integrated atom i (list slot k),
-// gathered from the terms of its neighbours' bonds that depend on x_i: the
-// bonds (a, i) (radial part and i as the partner in zeta_ai) and the bonds
-// (a, b) in which i is the third atom of zeta_ab.  (The terms of i's own
-// bonds come from pass 1.)
+// Any number of neighbours (lists in shared memory or in an overflow row):
+// one warp per centre, lane l owning neighbours l and l + 32.  The terms a
+// lane needs from the other neighbours are broadcast with shuffles; sums
+// over lanes use the fixed butterfly order.  All 32 lanes must call it with
+// the same slot.
 template <typename R, int TT>
-__device__ void ters_pass2(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& Fx, R& Fy, R& Fz)
+__device__ R ters_centre_warp(const HotParams<R>& H, Win<R, TT>& W, int k, int m, int nact,
+                              unsigned long long& triplets)
+{
+    const int lane = threadIdx.x & 31;
+    const int a = W.slot_atom[k];
+    const V4<R> pa = W.pos[a];
+    const uint16_t* row = W.list(k, m);
+    const uint8_t* rv = W.rev_row(k, m);
+    // per-neighbour terms of this lane's two neighbours (h = 0: lane, h = 1: lane + 32)
+    R ux[2], uy[2], uz[2], ir[2], rr[2], fc[2], dfc[2], P[2], Q[2], fx[2], fy[2], fz[2];
+    int id[2];
+    bool ok[2];
+    int npos = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = lane + 32 * h;
+        ok[h] = q < m;
+        ux[h] = uy[h] = uz[h] = ir[h] = rr[h] = fc[h] = dfc[h] = P[h] = Q[h] = R(0);
+        fx[h] = fy[h] = fz[h] = R(0);
+        id[h] = -1;
+        if (ok[h]) {
+            id[h] = row[q];
+            const V4<R> pq = W.pos[id[h]];
+            const R dx = pq.x - pa.x, dy = pq.y - pa.y, dz = pq.z - pa.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            ir[h] = Mth<R>::rsqrt(r2);
+            rr[h] = r2 * ir[h];
+            ux[h] = dx * ir[h];
+            uy[h] = dy * ir[h];
+            uz[h] = dz * ir[h];
+            fc[h] = ters_fc<R>(H, rr[h], dfc[h]);
+        }
+        npos += __popc(__ballot_sync(0xffffffffu, ok[h] && (fc[h] > R(0) || dfc[h] != R(0))));
+    }
+    if (lane == 0 && m > 1) triplets += (unsigned long long)((m - 1) * npos);
+    const bool two = m > 32;
+    // bond orders of this lane's bonds
+    R zeta[2] = {R(0), R(0)};
+    for (int p = 0; p < m; ++p) {
+        const int src = p & 31, hp = p >> 5;
+        const R vx = __shfl_sync(0xffffffffu, hp ? ux[1] : ux[0], src);
+        const R vy = __shfl_sync(0xffffffffu, hp ? uy[1] : uy[0], src);
+        const R vz = __shfl_sync(0xffffffffu, hp ? uz[1] : uz[0], src);
+        const R fp = __shfl_sync(0xffffffffu, hp ? fc[1] : fc[0], src);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            if (!ok[h] || lane + 32 * h == p || fp == R(0)) continue;
+            R dg;
+            zeta[h] += fp * ters_g<R>(H, ux[h] * vx + uy[h] * vy + uz[h] * vz, dg);
+        }
+    }
+    R E = R(0);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (ok[h] && (fc[h] > R(0) || dfc[h] != R(0))) {
+            R db, V, dV, pfa;
+            const R b = ters_b<R>(H, zeta[h], db);
+            ters_pair<R>(H, rr[h], fc[h], dfc[h], b, V, dV, pfa);
+            P[h] = R(0.5) * pfa * db;
+            Q[h] = R(0.5) * dV;
+            E += R(0.5) * V;
+        }
+    }
+    // forces on this lane's neighbours
+    R sg[2] = {R(0), R(0)};
+    for (int j = 0; j < m; ++j) {
+        const int src = j & 31, hj = j >> 5;
+        const R vx = __shfl_sync(0xffffffffu, hj ? ux[1] : ux[0], src);
+        const R vy = __shfl_sync(0xffffffffu, hj ? uy[1] : uy[0], src);
+        const R vz = __shfl_sync(0xffffffffu, hj ? uz[1] : uz[0], src);
+        const R fj = __shfl_sync(0xffffffffu, hj ? fc[1] : fc[0], src);
+        const R Pj = __shfl_sync(0xffffffffu, hj ? P[1] : P[0], src);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            if (!ok[h] || lane + 32 * h == j) continue;
+            const R cc = vx * ux[h] + vy * uy[h] + vz * uz[h];
+            R dg;
+            const R g = ters_g<R>(H, cc, dg);
+            sg[h] += Pj * g;
+            const R w = (Pj * fc[h] + P[h] * fj) * dg * ir[h];
+            fx[h] -= w * (vx - cc * ux[h]);
+            fy[h] -= w * (vy - cc * uy[h]);
+            fz[h] -= w * (vz - cc * uz[h]);
+        }
+    }
+    R ax = R(0), ay = R(0), az = R(0);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const R A = Q[h] + dfc[h] * sg[h];
+        fx[h] -= A * ux[h];
+        fy[h] -= A * uy[h];
+        fz[h] -= A * uz[h];
+        ax -= fx[h];
+        ay -= fy[h];
+        az -= fz[h];
+        if (ok[h]) {
+            const unsigned s = W.need_map[id[h]];
+            const uint8_t e = rv[lane + 32 * h];
+            if (s < (unsigned)nact && e != (uint8_t)REED_NO_REV) W.bf_store((int)s, e, fx[h], fy[h], fz[h]);
+        }
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    az = warp_sum(az);
+    E = warp_sum(E);
+    if (lane == 0 && k < nact) {
+        V4<R> f;
+        f.x = ax;
+        f.y = ay;
+        f.z = az;
+        f.w = R(0);
+        W.frc[a] = f;
+    }
+    return lane == 0 ? E : R(0);
+}
+
+// The centre pass over every needed slot (all threads; a barrier must follow).
+// Slots with at most REED_FAST_NB neighbours come first in `order` and take
+// one thread each; the rest take one warp each, handed out from the last
+// warp down (the last warps have the fewest thread-path slots).  Returns this
+// thread's share of the Tersoff energy.
+template <typename R, int TT>
+__device__ R ters_centres(const HotParams<R>& H, Win<R, TT>& W, unsigned long long& triplets)
+{
+    const int nneed = W.S->need_count, nact = W.S->active_count, nfast = W.S->nfast;
+    R E = R(0);
+    for (int j = threadIdx.x; j < nfast; j += blockDim.x) {
+        const int k = W.order[j];
+        E += ters_centre_fast<R, TT>(H, W, k, W.nnb[k], nact, triplets);
+    }
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    for (int j = nfast + (nw - 1 - w); j < nneed; j += nw) {
+        const int k = W.order[j];
+        E += ters_centre_warp<R, TT>(H, W, k, W.nnb[k], nact, triplets);
+    }
+    return E;
+}
+
+// Sum of the force row of the integrated atom in slot k (list order).
+template <typename R, int TT>
+__device__ __forceinline__ void ters_gather(const Win<R, TT>& W, int k, R& Fx, R& Fy, R& Fz)
 {
     const int m = W.nnb[k];
-    const uint16_t* nb = W.nbr + (size_t)k * REED_MAXNB;
-    const V4<R> pi = W.pos[i];
     R fx = R(0), fy = R(0), fz = R(0);
-    for (int q = 0; q < m; ++q) {
-        const int a = nb[q];
-        const V4<R> pa = W.pos[a];
-        const R dx = pa.x - pi.x, dy = pa.y - pi.y, dz = pa.z - pi.z;
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        const R ir = Mth<R>::rsqrt(r2);
-        const R ra = r2 * ir;
-        const R ux = dx * ir, uy = dy * ir, uz = dz * ir;   // unit i -> a
-        R dfa;
-        const R fa = ters_fc<R>(H, ra, dfa);
-        // terms centred on the neighbour a
-        const unsigned sa = W.need_map[a];
-        if (sa >= REED_PENDING) continue;
-        const int ma = W.nnb[sa];
-        const uint16_t* nba = W.nbr + (size_t)sa * REED_MAXNB;
-        const V2<R>* bond_a = W.bond + (size_t)sa * REED_MAXNB;
-        const R vx = -ux, vy = -uy, vz = -uz;   // unit a -> i
-        R ax = R(0), ay = R(0), az = R(0);      // d zeta_ai / d x_i
-        R pre_ai = R(0), dV_ai = R(0);
-        for (int p = 0; p < ma; ++p) {
-            const int b = nba[p];
-            const V2<R> bab = bond_a[p];
-            if (b == i) {
-                pre_ai = bab.a;
-                dV_ai = bab.b;
-                continue;
-            }
-            const V4<R> pb = W.pos[b];
-            const R wx0 = pb.x - pa.x, wy0 = pb.y - pa.y, wz0 = pb.z - pa.z;
-            const R r2b = wx0 * wx0 + wy0 * wy0 + wz0 * wz0;
-            const R irb = Mth<R>::rsqrt(r2b);
-            const R wx = wx0 * irb, wy = wy0 * irb, wz = wz0 * irb;   // unit a -> b
-            const R c = vx * wx + vy * wy + vz * wz;
-            R dg;
-            const R g = ters_g<R>(H, c, dg);
-            const R tx = (wx - c * vx) * ir, ty = (wy - c * vy) * ir, tz = (wz - c * vz) * ir;
-            R dfb;
-            const R fb = ters_fc<R>(H, r2b * irb, dfb);
-            ax += fb * dg * tx;
-            ay += fb * dg * ty;
-            az += fb * dg * tz;
-            // i as the third atom of zeta_ab
-            const R s1 = dfa * g, s2 = fa * dg;
-            fx -= bab.a * (s1 * vx + s2 * tx);
-            fy -= bab.a * (s1 * vy + s2 * ty);
-            fz -= bab.a * (s1 * vz + s2 * tz);
+    if (m <= REED_MAXNB) {
+        const int o = k * REED_BF_STRIDE;
+        for (int q = 0; q < m; ++q) {
+            fx += W.bfx[o + q];
+            fy += W.bfy[o + q];
+            fz += W.bfz[o + q];
         }
-        fx -= pre_ai * ax;
-        fy -= pre_ai * ay;
-        fz -= pre_ai * az;
-        fx += R(0.5) * dV_ai * ux;
-        fy += R(0.5) * dV_ai * uy;
-        fz += R(0.5) * dV_ai * uz;
+    } else {
+        const R* b = W.sp_bf + (size_t)W.nbr[(size_t)k * REED_MAXNB] * 3 * REED_SPILL_TERSOFF;
+        for (int q = 0; q < m; ++q) {
+            fx += b[q];
+            fy += b[REED_SPILL_TERSOFF + q];
+            fz += b[2 * REED_SPILL_TERSOFF + q];
+        }
     }
     Fx += fx;
     Fy += fy;
@@ -695,8 +987,8 @@ __device__ R pair_force(const HotParams<R>& H, Win<R, TT>& W, int i, int k, R& F
     const int m = W.nnb[k];
     const V4<R> pi = W.pos[i];
     const int si = species_of(pi);
-    const uint16_t* nb = W.nbr + (size_t)k * W.nb_slot;
-    const int oq = W.nb_q;
+    const uint16_t* nb = W.list(k, m);
+    const int oq = m <= maxnb(TT) ? W.nb_q : 1;   // an overflow row is contiguous
     R E = R(0);
     for (int q = 0; q < m; ++q) {
         const V4<R> pj = W.pos[nb[(size_t)q * oq]];
@@ -724,6 +1016,7 @@ template <typename R> struct Partial {
 struct WorkCount {
     unsigned long long triplets = 0;   // Tersoff bond-angle terms (one per zeta term)
     unsigned long long moved = 0;      // integrated atom updates
+    unsigned long long spilled = 0;    // overflow rows taken by list builds (thread 0)
 };
 
 // Force evaluation over the whole window; with KICK the second half kick is
@@ -776,7 +1069,7 @@ __device__ __forceinline__ void atom_force(const DevParams& P, const HotParams<R
     V4<R> p = W.pos[i];
     const bool act = is_active(p);
     R fx = R(0), fy = R(0), fz = R(0);
-    if (TT == REED_TT_TERSOFF && act && k >= 0) {   // own-bond terms from pass 1
+    if (TT == REED_TT_TERSOFF && act && k >= 0) {   // the bonds centred on i, from the centre pass
         const V4<R> f1 = W.frc[i];
         fx = f1.x;
         fy = f1.y;
@@ -800,7 +1093,7 @@ __device__ __forceinline__ void atom_force(const DevParams& P, const HotParams<R
     if (k >= 0) {
         if constexpr (TT == REED_TT_TERSOFF) {
             if (act) {
-                ters_pass2<R, TT>(H, W, i, k, fx, fy, fz);
+                ters_gather<R, TT>(W, k, fx, fy, fz);
                 out.bonds += W.nnb[k];
             }
         }
@@ -1182,12 +1475,12 @@ __device__ void initial_forces(const DevParams& P, const HotParams<R>& H, Win<R,
                                unsigned long long& ctr_rebuild, int& nbovf, int& capovf, WorkCount& wc)
 {
     if constexpr (TT != REED_TT_NONE) {
-        build_neighbours<R, TT>(P, H, W, nbovf, capovf);
+        build_neighbours<R, TT>(P, H, W, nbovf, capovf, wc.spilled);
         if (threadIdx.x == 0) ++ctr_rebuild;
         __syncthreads();
     }
     if constexpr (TT == REED_TT_TERSOFF) {
-        for (int k = threadIdx.x; k < W.S->need_count; k += blockDim.x) ters_pass1<R, TT>(H, W, k, wc.triplets);
+        ters_centres<R, TT>(H, W, wc.triplets);
         __syncthreads();
     }
     Partial<R> q = {R(0), R(0), R(0), R(0), R(0), R(0), 0, 0};
@@ -1232,7 +1525,8 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
 {
     static_assert(!ADJ || TT == REED_TT_NONE, "the adjoint runs without target-target forces");
     extern __shared__ __align__(16) unsigned char smem[];
-    Win<R, TT> W(smem, P.na, P.bond_cap, ADJ ? 1 : 0, P.g_nbins);
+    Win<R, TT> W(smem, P.na, P.bond_cap, ADJ ? 1 : 0, P.g_nbins, P.act_cap,
+                 B.spill ? B.spill + (size_t)blockIdx.x * B.spill_stride : nullptr);
     TrackShared<R>* S = W.S;
     const HotParams<R>& H = hot<R>(P);
     const int tid = threadIdx.x;
@@ -1346,7 +1640,7 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                 if (B.splits) atomicAdd(&B.splits[REED_MAX_THR], 1ull);
             }
             if constexpr (TT != REED_TT_NONE) {
-                build_neighbours<R, TT>(P, H, W, nbovf, capovf);
+                build_neighbours<R, TT>(P, H, W, nbovf, capovf, wc.spilled);
                 if (tid == 0) ++c_rebuild;
             }
             __syncthreads();
@@ -1360,7 +1654,7 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
             __syncthreads();
             if (tid == 0) S->top -= 1;
             if constexpr (TT != REED_TT_NONE) {
-                build_neighbours<R, TT>(P, H, W, nbovf, capovf);
+                build_neighbours<R, TT>(P, H, W, nbovf, capovf, wc.spilled);
                 if (tid == 0) ++c_rebuild;
             }
             __syncthreads();
@@ -1474,13 +1768,13 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                     m1 = fmax(m1, q1);
                 }
                 if (shift || m1 + m2 > H.skin) {
-                    build_neighbours<R, TT>(P, H, W, nbovf, capovf);
+                    build_neighbours<R, TT>(P, H, W, nbovf, capovf, wc.spilled);
                     __syncthreads();
                     if (tid == 0) ++c_rebuild;
                     lap(PH_BUILD);
                 }
                 if constexpr (TT == REED_TT_TERSOFF) {
-                    for (int k = tid; k < S->need_count; k += blockDim.x) ters_pass1<R, TT>(H, W, k, wc.triplets);
+                    ters_centres<R, TT>(H, W, wc.triplets);
                     __syncthreads();
                     lap(PH_PASS1);
                 }
@@ -1578,7 +1872,10 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                     if (tid == 0) {
                         c_drop += (unsigned long long)(nc - c);
                         atomicOr(B.status, ERR_QUEUE);
-                        S->ion.level += nc - c;   // keep weights consistent: the track carries all levels
+                        // the track still passes the levels (its depths stay in step with its
+                        // weight 2^-level), so the dropped clones' weight is lost from the
+                        // profile; the run reports REED_E_QUEUE_FULL
+                        S->ion.level += nc - c;
                     }
                     __syncthreads();
                     break;
@@ -1654,6 +1951,7 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
         if (tr) atomicAdd(&B.counters[C_TRIPLETS], tr);
         atomicAdd(&B.counters[C_MOVED], mv);
     }
+    if (tid == 0 && wc.spilled) atomicAdd(&B.counters[C_SPILLED], wc.spilled);
     if (tid == 0) {
         atomicAdd(&B.counters[C_PRIMARIES], c_prim);
         atomicAdd(&B.counters[C_CLONES], c_clone);

@@ -16,7 +16,6 @@ from . import build as _build
 
 OK = 0
 E_ARG, E_CUDA, E_TIMEOUT, E_QUEUE_FULL, E_NONFINITE, E_NOMEM, E_SMEM, E_STATE, E_NEIGHBOR = range(-1, -10, -1)
-W_NEIGHBOR = 1   # completed; some neighbour lists were truncated (stats["nb_overflow"])
 LATTICE = {"diamond": 0, "fluorite": 1}
 TT = {"none": 0, "tersoff": 1, "buckingham": 2}
 PREC_MIXED, PREC_FP64 = 0, 1
@@ -84,7 +83,8 @@ class reed_stats_t(C.Structure):
         "triplets", "atom_updates")] + [("phase_cycles", C.c_int64 * 6)] + \
         [("w_stopped", C.c_double), ("w_back", C.c_double), ("w_trunc", C.c_double), ("kernel_ms", C.c_double),
          ("threads_per_track", C.c_int32), ("ctas_per_sm", C.c_int32), ("grid", C.c_int32),
-         ("smem_bytes", C.c_int32), ("splits", C.c_int64 * 16), ("pooled", C.c_int64)]
+         ("smem_bytes", C.c_int32), ("splits", C.c_int64 * 16), ("pooled", C.c_int64),
+         ("nb_spilled", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -446,8 +446,8 @@ class Reed:
                                      float(w.get("sigma_amorphous", 0.0)))
 
     def run(self, n_ions=None, seed=None, precision=PREC_MIXED, tolerate=(), **kw):
-        """Run primaries; anomaly codes listed in `tolerate` (e.g. E_NEIGHBOR)
-        are returned instead of raised (the run is complete, see stats())."""
+        """Run primaries; error codes listed in `tolerate` (e.g. E_QUEUE_FULL)
+        are returned instead of raised (the run completed, see stats())."""
         w = dict(self.w, step_cap=kw.pop("step_cap", self.w["step_cap"]))
         o = run_opts(w, precision=precision, **kw)
         ion = w["ion"]

@@ -71,7 +71,7 @@ def test_binding_constants_match_the_header():
     src = open(os.path.join(ROOT, "include", "reed.h")).read()
     d = {k: int(v) for k, v in re.findall(r"#define REED_([A-Z0-9_]+)\s+(-?\d+)", src)}
     for name in ("OK", "E_ARG", "E_CUDA", "E_TIMEOUT", "E_QUEUE_FULL", "E_NONFINITE", "E_NOMEM", "E_SMEM",
-                 "E_STATE", "E_NEIGHBOR", "W_NEIGHBOR", "PREC_MIXED", "PREC_FP64"):
+                 "E_STATE", "E_NEIGHBOR", "PREC_MIXED", "PREC_FP64"):
         assert getattr(R, name) == d[name], name
     for table, prefix in ((R.LATTICE, "LATTICE_"), (R.TT, "TT_"), (R.BEAM, "BEAM_"), (R.TARGET, "TARGET_")):
         declared = {k[len(prefix):].lower(): v for k, v in d.items() if k.startswith(prefix)}

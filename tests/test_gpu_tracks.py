@@ -271,7 +271,7 @@ def test_limits_and_errors(R):
         with pytest.raises(R.ReedError) as e:
             ctx.run(n_ions=1, precision=1)
         assert e.value.code == R.E_SMEM
-        ctx.run(n_ions=2, seed=1, step_cap=300, tolerate=(R.W_NEIGHBOR,))
+        ctx.run(n_ions=2, seed=1, step_cap=300)
         st = ctx.stats()
         assert st["tracks"] == 2 and st["failed"] == 0
     w = workload("b1kev_si_0k_zbl")

@@ -9,7 +9,12 @@ point (reed_run + reed_range_profile) exactly, on two calls in a row (the
 shared scratch must not leak one call's state into the next), and that a
 configuration too large for the fixed scratch is refused.
 
-This file is collected last on purpose.
+The file is named to be collected last: it adds an entry point beside the
+main path rather than testing the main path, so a run that stops at the
+first failure (pytest -x) has already run every other test when this one
+fails.  The tests themselves do not depend on order: each passes alone in a
+fresh process and after the others (the scratch array is cleared by every
+call, and its device address is looked up per CUDA context).
 """
 import numpy as np
 import pytest

@@ -69,8 +69,8 @@ template <typename R> struct TrackShared {
     int shift, event, status, src, top, nclone, slot;
     int need_count, active_count;
     int nspill;           // overflow rows taken by the current lists
-    int nfast;            // Tersoff: slots of the unrolled path (the first nfast of `order`)
-    int scan[2][REED_MAX_WARPS];
+    int ncls[4];          // Tersoff: slots per centre-pass class, in `order` (see ters_centres)
+    int scan[4][REED_MAX_WARPS];
     long long pidx;
     R red[REED_MAX_WARPS][REED_NRED];
     R path2[REED_MAX_WARPS][2];   // per warp: the two longest atom paths since the list build
@@ -526,6 +526,43 @@ __device__ __forceinline__ void block_scan2(TrackShared<R>* S, int c0, int c1, i
     o1 = b1 + x1 - c1;
 }
 
+// The same for four counts (c[], offsets o[], totals t[]).
+template <typename R>
+__device__ __forceinline__ void block_scan4(TrackShared<R>* S, const int c[4], int o[4], int t[4])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int x[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = c[i];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int y = __shfl_up_sync(0xffffffffu, x[i], d);
+            if (lane >= d) x[i] += y;
+        }
+    }
+    __syncthreads();
+    if (lane == 31)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) S->scan[i][wid] = x[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int b = 0, tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w == wid) b = tot;
+            tot += S->scan[i][w];
+        }
+        o[i] = b + x[i] - c[i];
+        t[i] = tot;
+    }
+}
+
+// Centre-pass class of a Tersoff slot with m list neighbours: one thread
+// (unrolled, m <= REED_FAST_NB), or a group of 8, 16 or 32 lanes.
+__device__ __forceinline__ int centre_class(int m) { return m <= REED_FAST_NB ? 0 : (m <= 8 ? 1 : (m <= 16 ? 2 : 3)); }
+
 template <typename R, int TT>
 __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow,
                                  int& cap_overflow, unsigned long long& spilled)
@@ -664,18 +701,32 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
             rv[q] = e;
         }
     }
-    // the centre pass takes slots with at most REED_FAST_NB neighbours first
-    // (one thread each, unrolled), then the rest (one warp each)
+    // the centre pass takes the slots class by class (see ters_centres),
+    // in slot order inside a class
     {
         const int kc = (nneed + blockDim.x - 1) / blockDim.x;
         const int k0 = min(nneed, (int)threadIdx.x * kc), k1 = min(nneed, k0 + kc);
-        int nf = 0;
-        for (int k = k0; k < k1; ++k) nf += W.nnb[k] <= REED_FAST_NB;
-        int of, os, tf, ts;
-        block_scan2<R>(S, nf, (k1 - k0) - nf, of, os, tf, ts);
-        os += tf;
-        for (int k = k0; k < k1; ++k) W.order[W.nnb[k] <= REED_FAST_NB ? of++ : os++] = (uint16_t)k;
-        if (threadIdx.x == 0) S->nfast = tf;
+        int c[4] = {0, 0, 0, 0}, o[4], t[4];
+        for (int k = k0; k < k1; ++k) {
+            const int cl = centre_class(W.nnb[k]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) c[i] += cl == i;
+        }
+        block_scan4<R>(S, c, o, t);
+        o[1] += t[0];
+        o[2] += t[0] + t[1];
+        o[3] += t[0] + t[1] + t[2];
+        for (int k = k0; k < k1; ++k) {
+            const int cl = centre_class(W.nnb[k]);
+            int dst = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (cl == i) dst = o[i]++;
+            W.order[dst] = (uint16_t)k;
+        }
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) S->ncls[i] = t[i];
     }
     __syncthreads();
 }
@@ -807,28 +858,39 @@ __device__ __forceinline__ R ters_centre_fast(const HotParams<R>& H, Win<R, TT>&
     return E;
 }
 
-// Any number of neighbours (lists in shared memory or in an overflow row):
-// one warp per centre, lane l owning neighbours l and l + 32.  The terms a
-// lane needs from the other neighbours are broadcast with shuffles; sums
-// over lanes use the fixed butterfly order.  All 32 lanes must call it with
-// the same slot.
-template <typename R, int TT>
-__device__ R ters_centre_warp(const HotParams<R>& H, Win<R, TT>& W, int k, int m, int nact,
-                              unsigned long long& triplets)
+// More than REED_FAST_NB neighbours (lists in shared memory or in an
+// overflow row): a group of G lanes per centre (G = 8, 16 or 32; lane l of
+// the group owns neighbours l and, for G = 32, l + 32).  The terms a lane
+// needs from the other neighbours are broadcast with shuffles inside the
+// group; sums over the group use the fixed butterfly order.  All 32 lanes of
+// the warp call it together, each group with its own slot k (k < 0: idle).
+template <typename R, int TT, int G>
+__device__ R ters_centre_group(const HotParams<R>& H, Win<R, TT>& W, int k, int nact, unsigned long long& triplets)
 {
-    const int lane = threadIdx.x & 31;
-    const int a = W.slot_atom[k];
-    const V4<R> pa = W.pos[a];
-    const uint16_t* row = W.list(k, m);
-    const uint8_t* rv = W.rev_row(k, m);
-    // per-neighbour terms of this lane's two neighbours (h = 0: lane, h = 1: lane + 32)
-    R ux[2], uy[2], uz[2], ir[2], rr[2], fc[2], dfc[2], P[2], Q[2], fx[2], fy[2], fz[2];
-    int id[2];
-    bool ok[2];
+    constexpr int NH = G == 32 ? 2 : 1;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, lg = lane & (G - 1);
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int m = k >= 0 ? (int)W.nnb[k] : 0;
+    const int mmax = (int)__reduce_max_sync(FULL, (unsigned)m);
+    int a = 0;
+    V4<R> pa = {R(0), R(0), R(0), R(0)};
+    const uint16_t* row = nullptr;
+    const uint8_t* rv = nullptr;
+    if (k >= 0) {
+        a = W.slot_atom[k];
+        pa = W.pos[a];
+        row = W.list(k, m);
+        rv = W.rev_row(k, m);
+    }
+    // per-neighbour terms of this lane's neighbours
+    R ux[NH], uy[NH], uz[NH], ir[NH], rr[NH], fc[NH], dfc[NH], P[NH], Q[NH], fx[NH], fy[NH], fz[NH];
+    int id[NH];
+    bool ok[NH];
     int npos = 0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int q = lane + 32 * h;
+    for (int h = 0; h < NH; ++h) {
+        const int q = lg + G * h;
         ok[h] = q < m;
         ux[h] = uy[h] = uz[h] = ir[h] = rr[h] = fc[h] = dfc[h] = P[h] = Q[h] = R(0);
         fx[h] = fy[h] = fz[h] = R(0);
@@ -845,29 +907,29 @@ __device__ R ters_centre_warp(const HotParams<R>& H, Win<R, TT>& W, int k, int m
             uz[h] = dz * ir[h];
             fc[h] = ters_fc<R>(H, rr[h], dfc[h]);
         }
-        npos += __popc(__ballot_sync(0xffffffffu, ok[h] && (fc[h] > R(0) || dfc[h] != R(0))));
+        npos += __popc(__ballot_sync(FULL, ok[h] && (fc[h] > R(0) || dfc[h] != R(0))) & gmask);
     }
-    if (lane == 0 && m > 1) triplets += (unsigned long long)((m - 1) * npos);
-    const bool two = m > 32;
+    if (lg == 0 && m > 1) triplets += (unsigned long long)((m - 1) * npos);
     // bond orders of this lane's bonds
-    R zeta[2] = {R(0), R(0)};
-    for (int p = 0; p < m; ++p) {
-        const int src = p & 31, hp = p >> 5;
-        const R vx = __shfl_sync(0xffffffffu, hp ? ux[1] : ux[0], src);
-        const R vy = __shfl_sync(0xffffffffu, hp ? uy[1] : uy[0], src);
-        const R vz = __shfl_sync(0xffffffffu, hp ? uz[1] : uz[0], src);
-        const R fp = __shfl_sync(0xffffffffu, hp ? fc[1] : fc[0], src);
+    R zeta[NH];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1 && !two) break;
-            if (!ok[h] || lane + 32 * h == p || fp == R(0)) continue;
+    for (int h = 0; h < NH; ++h) zeta[h] = R(0);
+    for (int p = 0; p < mmax; ++p) {
+        const int src = p & (G - 1), hp = NH == 2 ? (p >> 5) : 0;
+        const R vx = __shfl_sync(FULL, hp ? ux[NH - 1] : ux[0], src, G);
+        const R vy = __shfl_sync(FULL, hp ? uy[NH - 1] : uy[0], src, G);
+        const R vz = __shfl_sync(FULL, hp ? uz[NH - 1] : uz[0], src, G);
+        const R fp = __shfl_sync(FULL, hp ? fc[NH - 1] : fc[0], src, G);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            if (!ok[h] || p >= m || lg + G * h == p || fp == R(0)) continue;
             R dg;
             zeta[h] += fp * ters_g<R>(H, ux[h] * vx + uy[h] * vy + uz[h] * vz, dg);
         }
     }
     R E = R(0);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NH; ++h) {
         if (ok[h] && (fc[h] > R(0) || dfc[h] != R(0))) {
             R db, V, dV, pfa;
             const R b = ters_b<R>(H, zeta[h], db);
@@ -878,18 +940,19 @@ __device__ R ters_centre_warp(const HotParams<R>& H, Win<R, TT>& W, int k, int m
         }
     }
     // forces on this lane's neighbours
-    R sg[2] = {R(0), R(0)};
-    for (int j = 0; j < m; ++j) {
-        const int src = j & 31, hj = j >> 5;
-        const R vx = __shfl_sync(0xffffffffu, hj ? ux[1] : ux[0], src);
-        const R vy = __shfl_sync(0xffffffffu, hj ? uy[1] : uy[0], src);
-        const R vz = __shfl_sync(0xffffffffu, hj ? uz[1] : uz[0], src);
-        const R fj = __shfl_sync(0xffffffffu, hj ? fc[1] : fc[0], src);
-        const R Pj = __shfl_sync(0xffffffffu, hj ? P[1] : P[0], src);
+    R sg[NH];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1 && !two) break;
-            if (!ok[h] || lane + 32 * h == j) continue;
+    for (int h = 0; h < NH; ++h) sg[h] = R(0);
+    for (int j = 0; j < mmax; ++j) {
+        const int src = j & (G - 1), hj = NH == 2 ? (j >> 5) : 0;
+        const R vx = __shfl_sync(FULL, hj ? ux[NH - 1] : ux[0], src, G);
+        const R vy = __shfl_sync(FULL, hj ? uy[NH - 1] : uy[0], src, G);
+        const R vz = __shfl_sync(FULL, hj ? uz[NH - 1] : uz[0], src, G);
+        const R fj = __shfl_sync(FULL, hj ? fc[NH - 1] : fc[0], src, G);
+        const R Pj = __shfl_sync(FULL, hj ? P[NH - 1] : P[0], src, G);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            if (!ok[h] || j >= m || lg + G * h == j) continue;
             const R cc = vx * ux[h] + vy * uy[h] + vz * uz[h];
             R dg;
             const R g = ters_g<R>(H, cc, dg);
@@ -902,7 +965,7 @@ __device__ R ters_centre_warp(const HotParams<R>& H, Win<R, TT>& W, int k, int m
     }
     R ax = R(0), ay = R(0), az = R(0);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NH; ++h) {
         const R A = Q[h] + dfc[h] * sg[h];
         fx[h] -= A * ux[h];
         fy[h] -= A * uy[h];
@@ -912,15 +975,18 @@ __device__ R ters_centre_warp(const HotParams<R>& H, Win<R, TT>& W, int k, int m
         az -= fz[h];
         if (ok[h]) {
             const unsigned s = W.need_map[id[h]];
-            const uint8_t e = rv[lane + 32 * h];
+            const uint8_t e = rv[lg + G * h];
             if (s < (unsigned)nact && e != (uint8_t)REED_NO_REV) W.bf_store((int)s, e, fx[h], fy[h], fz[h]);
         }
     }
-    ax = warp_sum(ax);
-    ay = warp_sum(ay);
-    az = warp_sum(az);
-    E = warp_sum(E);
-    if (lane == 0 && k < nact) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(FULL, ax, o);
+        ay += __shfl_xor_sync(FULL, ay, o);
+        az += __shfl_xor_sync(FULL, az, o);
+        E += __shfl_xor_sync(FULL, E, o);
+    }
+    if (lg == 0 && k >= 0 && k < nact) {
         V4<R> f;
         f.x = ax;
         f.y = ay;
@@ -928,27 +994,38 @@ __device__ R ters_centre_warp(const HotParams<R>& H, Win<R, TT>& W, int k, int m
         f.w = R(0);
         W.frc[a] = f;
     }
-    return lane == 0 ? E : R(0);
+    return (lg == 0 && k >= 0) ? E : R(0);
 }
 
 // The centre pass over every needed slot (all threads; a barrier must follow).
-// Slots with at most REED_FAST_NB neighbours come first in `order` and take
-// one thread each; the rest take one warp each, handed out from the last
-// warp down (the last warps have the fewest thread-path slots).  Returns this
-// thread's share of the Tersoff energy.
+// `order` holds the slots class by class: ncls[0] with at most REED_FAST_NB
+// neighbours (one thread each, unrolled), then ncls[1] with up to 8 (groups
+// of 8 lanes, four centres per warp), ncls[2] with up to 16 (two per warp)
+// and ncls[3] with more (one per warp).  The group tasks are dealt to the
+// warps from the last one down (the last warps have the fewest one-thread
+// slots).  Returns this thread's share of the Tersoff energy.
 template <typename R, int TT>
 __device__ R ters_centres(const HotParams<R>& H, Win<R, TT>& W, unsigned long long& triplets)
 {
-    const int nneed = W.S->need_count, nact = W.S->active_count, nfast = W.S->nfast;
+    const int nact = W.S->active_count;
+    const int n0 = W.S->ncls[0], n1 = W.S->ncls[1], n2 = W.S->ncls[2], n3 = W.S->ncls[3];
     R E = R(0);
-    for (int j = threadIdx.x; j < nfast; j += blockDim.x) {
+    for (int j = threadIdx.x; j < n0; j += blockDim.x) {
         const int k = W.order[j];
         E += ters_centre_fast<R, TT>(H, W, k, W.nnb[k], nact, triplets);
     }
-    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-    for (int j = nfast + (nw - 1 - w); j < nneed; j += nw) {
-        const int k = W.order[j];
-        E += ters_centre_warp<R, TT>(H, W, k, W.nnb[k], nact, triplets);
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t1 = (n1 + 3) / 4, t2 = (n2 + 1) / 2, ntask = t1 + t2 + n3;
+    for (int t = nw - 1 - w; t < ntask; t += nw) {
+        if (t < t1) {
+            const int j = 4 * t + (lane >> 3);
+            E += ters_centre_group<R, TT, 8>(H, W, j < n1 ? (int)W.order[n0 + j] : -1, nact, triplets);
+        } else if (t < t1 + t2) {
+            const int j = 2 * (t - t1) + (lane >> 4);
+            E += ters_centre_group<R, TT, 16>(H, W, j < n2 ? (int)W.order[n0 + n1 + j] : -1, nact, triplets);
+        } else {
+            E += ters_centre_group<R, TT, 32>(H, W, (int)W.order[n0 + n1 + n2 + (t - t1 - t2)], nact, triplets);
+        }
     }
     return E;
 }

@@ -174,8 +174,8 @@ typedef struct {
     int32_t reserved3;
     double damage_voxel;       /* A */
     double damage_min;         /* eV */
-    /* Truncated-segment sensitivities (target model NONE, no cloning, records
-     * on): for every stopped track, dz_T/dtheta for theta = (s_e, s_loc,
+    /* Truncated-segment sensitivities (target model NONE, frozen_margin 0,
+     * no cloning, records on): for every stopped track, dz_T/dtheta for theta = (s_e, s_loc,
      * spline_c[0..5]) through its last adj_segment steps (the state
      * adj_segment..adj_segment+adj_every-1 steps before the end held fixed),
      * with dt, window moves and the drag's on/off frozen; checkpoints every

@@ -247,8 +247,7 @@ __device__ void replay_step(const DevParams& P, const HotParams<R>& H, Win<R, TT
     const int shift = S->shift;
     for (int i = threadIdx.x; i < P.na; i += blockDim.x) {
         V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
-        if (shift) reanchor_atom<R>(P, H, S->ion.key, i, S->Aold, S->ion.A, p, v, f);
-        if (is_active(p)) {
+        if (is_active(p)) {   // (kick and drift precede the window move, as in the forward step)
             const R k = hdt * H.invM2[species_of(p)];
             v.x += k * f.x;
             v.y += k * f.y;
@@ -257,6 +256,7 @@ __device__ void replay_step(const DevParams& P, const HotParams<R>& H, Win<R, TT
             p.y += dt * v.y;
             p.z += dt * v.z;
         }
+        if (shift) reanchor_atom<R>(P, H, S->ion.key, i, S->Aold, S->ion.A, p, v, f);
         W.pos[i] = p;
         W.vel[i] = v;
         if (shift) W.frc[i] = f;

@@ -701,6 +701,8 @@ int reed_run(reed_ctx* ctx, double ion_Z, double ion_M, double energy_eV, double
     if (o.adjoint) {
         if (tt != REED_TT_NONE || P.nthr > 0 || o.adaptive || !o.record_tracks)
             return fail(ctx, REED_E_ARG, "adjoint runs need target model NONE, no cloning and record_tracks");
+        // (the reverse pass treats every atom of the window as integrated)
+        if (P.margin != 0) return fail(ctx, REED_E_ARG, "adjoint runs need frozen_margin 0");
         const int seg = o.adj_segment > 0 ? o.adj_segment : 200, every = o.adj_every > 0 ? o.adj_every : 20;
         if (seg % every != 0 || seg + every > REED_STEP_RING_HOST)
             return fail(ctx, REED_E_ARG, "adj_segment must be a multiple of adj_every and adj_segment + adj_every <= %d",

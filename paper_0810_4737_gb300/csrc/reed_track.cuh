@@ -449,17 +449,27 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
     const int nb = P.g_nb;
     const int bx = grid_axis<R>(P, H, pi.x), by = grid_axis<R>(P, H, pi.y), bz = grid_axis<R>(P, H, pi.z);
     const int z0 = max(bz - 1, 0), z1 = min(bz + 1, nb - 1);
+    // (candidates are read four at a time so that their loads overlap: the
+    // search is bound by shared-memory latency, not by arithmetic)
     for (int cx = max(bx - 1, 0); cx <= min(bx + 1, nb - 1); ++cx) {
         for (int cy = max(by - 1, 0); cy <= min(by + 1, nb - 1); ++cy) {
             // bins z0..z1 of one (x, y) column are consecutive in binned[]
             const int col = (cx * nb + cy) * nb;
             const int q1 = W.bin_start[col + z1 + 1];
-            for (int q = W.bin_start[col + z0]; q < q1; ++q) {
-                const int j = W.binned[q];
-                if (j == i) continue;
-                const V4<R> pj = W.pos[j];
-                const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                if (dx * dx + dy * dy + dz * dz < H.rlist2) {
+            for (int q0 = W.bin_start[col + z0]; q0 < q1; q0 += 4) {
+                int jj[4];
+                V4<R> pp[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) jj[u] = q0 + u < q1 ? (int)W.binned[q0 + u] : i;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) pp[u] = W.pos[jj[u]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = jj[u];
+                    if (j == i) continue;
+                    const V4<R> pj = pp[u];
+                    const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    if (!(dx * dx + dy * dy + dz * dz < H.rlist2)) continue;
                     if (cnt < NS) {
                         out[(size_t)cnt * oq] = (uint16_t)j;
                         ++cnt;
@@ -681,24 +691,37 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
     // reverse entries: where the centre of slot k sits in the list of each
     // integrated neighbour (lists are symmetric: the same distance test from
     // both ends), so the centre pass can leave its force there
+    // (four entries at a time, and the neighbour's list four entries at a
+    // time, so that the dependent shared-memory loads overlap)
     for (int k = threadIdx.x; k < nneed; k += blockDim.x) {
         const int a = W.slot_atom[k], m = W.nnb[k];
         const uint16_t* row = W.list(k, m);
         uint8_t* rv = W.rev_row(k, m);
-        for (int q = 0; q < m; ++q) {
-            const unsigned sp = W.need_map[row[q]];
-            uint8_t e = (uint8_t)REED_NO_REV;
-            if (sp < (unsigned)nact_slots) {
-                const int mp = W.nnb[sp];
-                const uint16_t* prow = W.list((int)sp, mp);
-                for (int t = 0; t < mp; ++t)
-                    if (prow[t] == a) {
-                        e = (uint8_t)t;
-                        break;
+        for (int q0 = 0; q0 < m; q0 += 4) {
+            unsigned sp[4];
+            int mp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sp[u] = q0 + u < m ? (unsigned)W.need_map[row[q0 + u]] : REED_NO_SLOT;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) mp[u] = sp[u] < (unsigned)nact_slots ? (int)W.nnb[sp[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (q0 + u >= m) break;
+                uint8_t e = (uint8_t)REED_NO_REV;
+                if (sp[u] < (unsigned)nact_slots) {
+                    const uint16_t* prow = W.list((int)sp[u], mp[u]);
+                    for (int t0 = 0; t0 < mp[u] && e == (uint8_t)REED_NO_REV; t0 += 4) {
+                        int pv[4];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) pv[v] = t0 + v < mp[u] ? (int)prow[t0 + v] : -1;
+#pragma unroll
+                        for (int v = 3; v >= 0; --v)
+                            if (pv[v] == a) e = (uint8_t)(t0 + v);
                     }
-                if (e == (uint8_t)REED_NO_REV) ++overflow;   // only with a truncated list
+                    if (e == (uint8_t)REED_NO_REV) ++overflow;   // only with a truncated list
+                }
+                rv[q0 + u] = e;
             }
-            rv[q] = e;
         }
     }
     // the centre pass takes the slots class by class (see ters_centres),
@@ -1758,6 +1781,19 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                 // the same operations as the separate phases of the other models
                 for (int i = tid; i < P.na; i += blockDim.x) {
                     V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
+                    // half kick and drift of the atoms integrated before the
+                    // window moves, then the move (a step's kick and drift
+                    // precede its window update)
+                    if (is_active(p)) {
+                        ++wc.moved;
+                        const R k = hdt * H.invM2[species_of(p)];
+                        v.x += k * f.x;
+                        v.y += k * f.y;
+                        v.z += k * f.z;
+                        p.x += dt * v.x;
+                        p.y += dt * v.y;
+                        p.z += dt * v.z;
+                    }
                     if (shift) {
                         const V4<R> p0 = p, v0 = v;
                         if (reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f))
@@ -1772,16 +1808,6 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                         continue;
                     }
                     const bool act = is_active(p);
-                    if (act) {
-                        ++wc.moved;
-                        const R k = hdt * H.invM2[species_of(p)];
-                        v.x += k * f.x;
-                        v.y += k * f.y;
-                        v.z += k * f.z;
-                        p.x += dt * v.x;
-                        p.y += dt * v.y;
-                        p.z += dt * v.z;
-                    }
                     ion_atom_step<R>(P, H, W.S, p, v, act, hdt, f, q);
                     W.pos[i] = p;
                     W.vel[i] = v;
@@ -1791,15 +1817,14 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                 __syncthreads();
                 lap(PH_FORCE);
             } else {
-            // phase A: re-anchor and first half kick + drift of own atoms
+            // phase A: first half kick + drift of the atoms integrated before
+            // the window moves, then the move (a step's kick and drift precede
+            // its window update: an atom entering the integrated region is
+            // first kicked at the end of this step, one leaving it still
+            // moves in this step)
             R pm1 = R(0), pm2 = R(0);   // this thread's two longest paths
             for (int i = tid; i < P.na; i += blockDim.x) {
                 V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
-                if (shift) {
-                    const V4<R> p0 = p, v0 = v;
-                    if (reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f))
-                        deposit_damage<R>(P, B, p0, v0, S->Aold, ldexp(1.0, -S->ion.level));
-                }
                 if (is_active(p)) {
                     ++wc.moved;
                     const R k = hdt * H.invM2[species_of(p)];
@@ -1819,6 +1844,11 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                             pm2 = v.w;
                         }
                     }
+                }
+                if (shift) {
+                    const V4<R> p0 = p, v0 = v;
+                    if (reanchor_atom<R>(P, H, key, i, S->Aold, S->ion.A, p, v, f))
+                        deposit_damage<R>(P, B, p0, v0, S->Aold, ldexp(1.0, -S->ion.level));
                 }
                 W.pos[i] = p;
                 W.vel[i] = v;

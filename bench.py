@@ -401,7 +401,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "stats": {k: st[k] for k in ("primaries", "tracks", "steps", "pair_evals", "bond_evals", "triplets",
-                                         "atom_updates", "shifts", "rebuilds", "nb_overflow", "bond_cap_overflow", "nb_spilled",
+                                         "atom_updates", "shifts", "rebuilds", "list_refreshes", "nb_overflow", "bond_cap_overflow", "nb_spilled",
                                          "threads_per_track", "ctas_per_sm", "grid", "smem_bytes", "phase_cycles")},
         }
         print(json.dumps(line), flush=True)

@@ -183,11 +183,16 @@ typedef struct {
     int32_t adjoint;
     int32_t adj_segment;
     int32_t adj_every;
-    int32_t reserved4;
+    /* Self-check of the target neighbour lists (slow; for tests): after
+     * every build and refresh each list is compared with a brute-force
+     * search over the window; differences are counted in nl_check_errors. */
+    int32_t nl_check;
     /* Target neighbour lists (Tersoff, Buckingham): list radius = cutoff +
-     * nl_skin; a list is rebuilt after a window move and when the two longest
-     * atom paths since the last build add up to more than nl_skin.  0 = 0.2 A
-     * for Tersoff, 0.3 A for the pair lists. */
+     * nl_skin; the lists are rebuilt after a window move and when the two
+     * longest atom paths since their last list add up to more than nl_skin
+     * (Tersoff: then only the lists of atoms whose path exceeds nl_skin / 2
+     * are recomputed, and the entries of the others that involve them).
+     * 0 = 0.2 A for Tersoff, 0.3 A for the pair lists. */
     double nl_skin;
     /* Energy term of the adaptive step (the paper's step rule in terms of the
      * kinetic and collisional energy, Sec. 2): when > 0, also
@@ -242,6 +247,10 @@ typedef struct {
                                 (taken from the shared clone pool) */
     int64_t nb_spilled;      /* lists that outgrew their shared-memory row and moved whole
                                 to an overflow row in global memory (exact, only slower) */
+    int64_t list_refreshes;  /* Tersoff partial list refreshes (only the lists of atoms that
+                                moved more than half the skin recomputed) */
+    int64_t nl_check_errors; /* with opt->nl_check: list entries that differ from a
+                                brute-force search (0 when the lists are exact) */
 } reed_stats_t;
 
 typedef struct reed_ctx reed_ctx;

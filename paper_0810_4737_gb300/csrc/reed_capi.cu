@@ -358,12 +358,15 @@ int make_params(reed_ctx* ctx, DevParams& P, double Z1, double M1, double E, dou
     P.de_max = o.de_max > 0.0 ? o.de_max : 0.0;
     P.dx_min = o.dx_min > 0.0 ? std::min(o.dx_min, o.dx_max) : std::min(1e-4, o.dx_max);
     P.pool_polls = o.pool_poll_limit > 0 ? o.pool_poll_limit : (1ll << 26);
+    P.nl_check = o.nl_check ? 1 : 0;
     const double skin = o.nl_skin > 0.0 ? o.nl_skin : (P.tt == REED_TT_TERSOFF ? kSkinTersoff : kSkinPairs);
     // neighbour-search grid over the window: bins no narrower than the list
-    // radius (with a margin for rounding), at most 10 per axis
+    // radius (with a margin for rounding) -- for Tersoff, whose lists are
+    // refreshed between builds on the bins of the last build, than the list
+    // radius plus half the skin -- at most 10 per axis
     {
         const double rl = (P.tt == REED_TT_BUCKINGHAM ? ctx->pot.buck_cut[1]
-                                                     : ctx->pot.tersoff[9] + ctx->pot.tersoff[10]) + skin;
+                                                     : ctx->pot.tersoff[9] + ctx->pot.tersoff[10] + 0.5 * skin) + skin;
         P.g_nb = std::max(1, std::min(10, (int)std::floor(P.n * P.a / (rl * 1.001))));
         P.g_nbins = P.g_nb * P.g_nb * P.g_nb;
     }
@@ -959,6 +962,8 @@ int reed_stats(reed_ctx* ctx, reed_stats_t* out)
     out->nb_overflow = (int64_t)c[C_NBOVF];
     out->bond_cap_overflow = (int64_t)c[C_CAPOVF];
     out->nb_spilled = (int64_t)c[C_SPILLED];
+    out->list_refreshes = (int64_t)c[C_REFRESH];
+    out->nl_check_errors = (int64_t)c[C_NLCHECK];
     out->triplets = (int64_t)c[C_TRIPLETS];
     out->atom_updates = (int64_t)c[C_MOVED];
     for (int k = 0; k < REED_NPHASE; ++k) out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
@@ -1663,6 +1668,8 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
         stats_out->nb_overflow = (int64_t)c[C_NBOVF];
         stats_out->bond_cap_overflow = (int64_t)c[C_CAPOVF];
         stats_out->nb_spilled = (int64_t)c[C_SPILLED];
+        stats_out->list_refreshes = (int64_t)c[C_REFRESH];
+        stats_out->nl_check_errors = (int64_t)c[C_NLCHECK];
         stats_out->failed = (int64_t)c[C_FAILED];
         stats_out->stopped = (int64_t)c[C_STOP];
         stats_out->backscattered = (int64_t)c[C_BACK];

@@ -28,6 +28,8 @@
 #define REED_SPILL_ROWS 32      // overflow rows per CTA
 #define REED_SPILL_TERSOFF 64   // entries of a Tersoff overflow row
 #define REED_SPILL_PAIR 192     // entries of a pair-list overflow row
+#define REED_MAX_HOT 30         // Tersoff partial refresh: atoms whose lists one refresh recomputes
+#define REED_MAX_STALE 128      // ... and atoms whose grid bins may be stale since the last full build
 
 // neighbour-list capacity per atom in shared memory, and of an overflow row
 __host__ __device__ constexpr int maxnb(int tt) { return tt == REED_TT_BUCKINGHAM ? REED_MAXNB_PAIR : REED_MAXNB; }
@@ -41,14 +43,15 @@ __host__ __device__ constexpr int spill_width(int tt)
 //   -1 for an empty slot (cell above the surface).
 #define REED_W_EMPTY (-1)
 
-enum { REED_NCOUNT = 25 };
+enum { REED_NCOUNT = 27 };
 enum { REED_NRED = 9 };   // per-warp partial sums of a force pass
 // cycle counters of the step phases (thread 0 of every CTA, summed)
 enum { PH_ION = 0, PH_MOVE, PH_BUILD, PH_PASS1, PH_FORCE, PH_ADMIN, REED_NPHASE };
 #define C_PHASE0 C_SPARE
 enum {
     C_PRIMARIES = 0, C_CLONES, C_TRACKS, C_STEPS, C_PAIRS, C_BONDS, C_SHIFTS, C_REBUILDS,
-    C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_CAPOVF, C_TRIPLETS, C_MOVED, C_SPILLED, C_SPARE
+    C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_CAPOVF, C_TRIPLETS, C_MOVED, C_SPILLED, C_REFRESH,
+    C_NLCHECK, C_SPARE
 };   // C_SPARE .. C_SPARE + REED_NPHASE - 1 hold the phase clocks
 enum { W_STOPPED = 0, W_BACK, W_TRUNC, W_FAILED };
 
@@ -104,6 +107,7 @@ struct DevParams {
     double b_rt, b_rc, b_lo, b_hi;
     double b_zk[3], b_zia[3];
     int bond_cap;                      // neighbour-list rows (Tersoff: needed atoms)
+    int nl_check;                      // compare every list with a brute-force search after each build
     int act_cap;                       // integrated atoms a window can hold (rows of the per-bond forces)
     // electronic stopping (Sec. 2 "Third")
     double gamma, s_loc, rho0_inv, lam_inv;

@@ -70,6 +70,11 @@ template <typename R> struct TrackShared {
     int need_count, active_count;
     int nspill;           // overflow rows taken by the current lists
     int ncls[4];          // Tersoff: slots per centre-pass class, in `order` (see ters_centres)
+    // Tersoff partial refreshes: atoms whose bins are stale since the last
+    // full build (atom order), and the atoms refreshed now
+    int nstale, nhot;
+    uint16_t stale[REED_MAX_STALE];
+    uint16_t hot[REED_MAX_HOT];
     int scan[4][REED_MAX_WARPS];
     long long pidx;
     R red[REED_MAX_WARPS][REED_NRED];
@@ -104,17 +109,19 @@ template <typename R, int TT> struct Layout {
                align(cap) +                              // nnb
                align(sizeof(uint16_t) * cap * maxnb(TT));     // nbr
     }
-    static __host__ __device__ size_t bond_bytes(int cap, int act)
+    static __host__ __device__ size_t bond_bytes(int cap, int act, int na = 0)
     {
         if (TT != REED_TT_TERSOFF) return 0;
-        return align((size_t)cap * REED_MAXNB) +                       // rev
+        return 2 * align(sizeof(unsigned) * (size_t)((na + 31) / 32)) + // stale and hot bits
+               align(sizeof(unsigned) * (size_t)cap) +                 // refresh marks per slot
+               align((size_t)cap * REED_MAXNB) +                       // rev
                align(sizeof(uint16_t) * cap) +                         // order
                3 * align(sizeof(R) * (size_t)act * REED_BF_STRIDE);    // per-bond forces (x, y, z)
     }
     static __host__ __device__ size_t adj_bytes(int na, int adj) { return adj ? 2 * align(sizeof(V4<R>) * na) : 0; }
     static __host__ __device__ size_t total(int na, int cap, int adj = 0, int nbins = 0, int act = 0)
     {
-        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap, nbins) + bond_bytes(cap, act) +
+        return shared_bytes() + atoms_bytes(na) + nbr_bytes(na, cap, nbins) + bond_bytes(cap, act, na) +
                adj_bytes(na, adj);
     }
     // bytes of one clone record: ion header + pos, vel, frc
@@ -147,6 +154,10 @@ template <typename R, int TT> struct Win {
     uint16_t* slot_atom;  // list slot -> atom
     uint8_t* nnb;         // neighbours per slot
     uint16_t* nbr;        // neighbour atoms per slot
+    unsigned* sbits;      // Tersoff: atoms whose grid bin is stale (one bit each)
+    unsigned* hbits;      // Tersoff: atoms refreshed by the current partial refresh
+    unsigned* tmask;      // Tersoff refresh, per slot: bit 31 = row rebuilt or loses a hot atom, bit t < 30 =
+                          //   gains hot atom t, bit 30 = lists a changed row
     uint8_t* rev;         // Tersoff: per slot and neighbour, the centre's entry in the neighbour's list
     uint16_t* order;      // Tersoff: slots in the order the centre pass takes them
     R* bfx;               // Tersoff: per integrated slot and list entry, the force of the
@@ -188,6 +199,7 @@ template <typename R, int TT> struct Win {
         slot_atom = nullptr;
         nnb = nullptr;
         nbr = nullptr;
+        sbits = hbits = tmask = nullptr;
         rev = nullptr;
         order = nullptr;
         bfx = bfy = bfz = nullptr;
@@ -212,6 +224,12 @@ template <typename R, int TT> struct Win {
             if (spill) sp_nbr = reinterpret_cast<uint16_t*>(spill);
         }
         if constexpr (TT == REED_TT_TERSOFF) {
+            const size_t bw = L::align(sizeof(unsigned) * (size_t)((na + 31) / 32));
+            sbits = reinterpret_cast<unsigned*>(base + o);
+            hbits = reinterpret_cast<unsigned*>(base + o + bw);
+            o += 2 * bw;
+            tmask = reinterpret_cast<unsigned*>(base + o);
+            o += L::align(sizeof(unsigned) * (size_t)cap);
             rev = base + o;
             o += L::align((size_t)cap * REED_MAXNB);
             order = reinterpret_cast<uint16_t*>(base + o);
@@ -431,21 +449,73 @@ __device__ __forceinline__ int grid_bin(const DevParams& P, const HotParams<R>& 
     return (grid_axis<R>(P, H, p.x) * P.g_nb + grid_axis<R>(P, H, p.y)) * P.g_nb + grid_axis<R>(P, H, p.z);
 }
 
+// Squared distance in a fixed operation order (no contraction), so that a
+// pair's list test gives the same answer from both ends in every list
+// builder: the lists are symmetric.
+__device__ __forceinline__ float list_d2(const V4<float>& a, const V4<float>& b)
+{
+    const float dx = __fsub_rn(b.x, a.x), dy = __fsub_rn(b.y, a.y), dz = __fsub_rn(b.z, a.z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+__device__ __forceinline__ double list_d2(const V4<double>& a, const V4<double>& b)
+{
+    const double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y), dz = __dsub_rn(b.z, a.z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+__device__ __forceinline__ bool bit_of(const unsigned* b, int i) { return (b[i >> 5] >> (i & 31)) & 1u; }
+
+// Appends neighbours to the list of one slot: the shared row, then -- past
+// its capacity -- a whole overflow row in global memory; past that, entries
+// are dropped and counted in `overflow` (which fails the run).
+template <typename R, int TT> struct ListWriter {
+    uint16_t* out;
+    int oq;
+    uint16_t* sp = nullptr;
+    bool asked = false;
+    int cnt = 0;
+    __device__ ListWriter(Win<R, TT>& W, int slot) : out(W.nbr + (size_t)slot * W.nb_slot), oq(W.nb_q) {}
+    __device__ __forceinline__ void add(Win<R, TT>& W, int j, int& overflow)
+    {
+        constexpr int NS = maxnb(TT), NW = spill_width(TT);
+        if (cnt < NS) {
+            out[(size_t)cnt * oq] = (uint16_t)j;
+            ++cnt;
+            return;
+        }
+        if (!asked && W.sp_nbr) {
+            asked = true;
+            const int r = atomicAdd(&W.S->nspill, 1);
+            if (r < REED_SPILL_ROWS) {
+                sp = W.sp_nbr + (size_t)r * NW;
+                for (int e = 0; e < NS; ++e) sp[e] = out[(size_t)e * oq];
+                out[0] = (uint16_t)r;
+            }
+        }
+        if (sp && cnt < NW) {
+            sp[cnt] = (uint16_t)j;
+            ++cnt;
+        } else {
+            ++overflow;
+        }
+    }
+};
+
 // Neighbours of atom i within the list radius, in bin order, into list slot
 // `slot`.  Past the shared row's capacity the list moves to an overflow row
 // in global memory; past that row's capacity (or with no row left) the
 // entries are dropped and counted in `overflow`, which fails the run.
-template <typename R, int TT>
+// MODE 0: every atom; atoms whose bins are stale (Tersoff partial refreshes)
+// are skipped in the bins and tested from the stale set instead.  MODE 1
+// (lists of atoms that became needed in a partial refresh): frozen atoms from
+// the bins, then the atoms being refreshed.
+template <typename R, int TT, int MODE = 0>
 __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int i, int slot,
                                       int& overflow)
 {
-    constexpr int NS = maxnb(TT), NW = spill_width(TT);
     const V4<R> pi = W.pos[i];
-    uint16_t* out = W.nbr + (size_t)slot * W.nb_slot;
-    const int oq = W.nb_q;
-    uint16_t* sp = nullptr;   // overflow row, once the shared row is full
-    bool asked = false;
-    int cnt = 0;
+    ListWriter<R, TT> L(W, slot);
+    bool skip_stale = false;
+    if constexpr (TT == REED_TT_TERSOFF) skip_stale = MODE == 0 && W.S->nstale > 0;
     const int nb = P.g_nb;
     const int bx = grid_axis<R>(P, H, pi.x), by = grid_axis<R>(P, H, pi.y), bz = grid_axis<R>(P, H, pi.z);
     const int z0 = max(bz - 1, 0), z1 = min(bz + 1, nb - 1);
@@ -468,35 +538,146 @@ __device__ __forceinline__ int list_of(const DevParams& P, const HotParams<R>& H
                     const int j = jj[u];
                     if (j == i) continue;
                     const V4<R> pj = pp[u];
-                    const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                    if (!(dx * dx + dy * dy + dz * dz < H.rlist2)) continue;
-                    if (cnt < NS) {
-                        out[(size_t)cnt * oq] = (uint16_t)j;
-                        ++cnt;
-                    } else {
-                        if (!asked && W.sp_nbr) {
-                            asked = true;
-                            const int r = atomicAdd(&W.S->nspill, 1);
-                            if (r < REED_SPILL_ROWS) {
-                                sp = W.sp_nbr + (size_t)r * NW;
-                                for (int e = 0; e < NS; ++e) sp[e] = out[(size_t)e * oq];
-                                out[0] = (uint16_t)r;
-                            }
-                        }
-                        if (sp && cnt < NW) {
-                            sp[cnt] = (uint16_t)j;
-                            ++cnt;
-                        } else {
-                            ++overflow;
-                        }
-                    }
+                    if (MODE == 1 && is_active(pj)) continue;
+                    if (skip_stale && bit_of(W.sbits, j)) continue;
+                    if (!(list_d2(pi, pj) < H.rlist2)) continue;
+                    L.add(W, j, overflow);
                     if (TT == REED_TT_TERSOFF && !is_active(pj) && W.need_map[j] == REED_NO_SLOT)
                         W.need_map[j] = (uint16_t)REED_PENDING;
                 }
             }
         }
     }
-    return cnt;
+    if constexpr (TT == REED_TT_TERSOFF) {
+        const int ns = MODE == 0 ? (skip_stale ? W.S->nstale : 0) : W.S->nhot;
+        const uint16_t* set = MODE == 0 ? W.S->stale : W.S->hot;
+        for (int t = 0; t < ns; ++t) {
+            const int j = set[t];
+            if (j == i) continue;
+            const V4<R> pj = W.pos[j];
+            if (!(list_d2(pi, pj) < H.rlist2)) continue;
+            L.add(W, j, overflow);
+            if (!is_active(pj) && W.need_map[j] == REED_NO_SLOT) W.need_map[j] = (uint16_t)REED_PENDING;
+        }
+    }
+    return L.cnt;
+}
+
+// The same search by one warp (all 32 lanes call it with the same i; Tersoff
+// lists): lanes take the candidates in the order list_of visits them (bin
+// columns, then the stale or hot set), ballots keep that order.  Used where
+// a few lists are built while the rest of the CTA waits.  An overflow row
+// the slot held before is reused.
+template <typename R, int TT, int MODE>
+__device__ int list_of_warp(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int i, int slot, int& overflow)
+{
+    constexpr int NS = REED_MAXNB, NW = REED_SPILL_TERSOFF;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const V4<R> pi = W.pos[i];
+    const bool skip_stale = MODE == 0 && W.S->nstale > 0;
+    const int nb = P.g_nb;
+    const int bx = grid_axis<R>(P, H, pi.x), by = grid_axis<R>(P, H, pi.y), bz = grid_axis<R>(P, H, pi.z);
+    const int z0 = max(bz - 1, 0), z1 = min(bz + 1, nb - 1);
+    // the candidate columns: ranges [qs, qs + len) of binned[], in visiting order
+    int qs[9], pre[10];
+    pre[0] = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const int cx = bx - 1 + c / 3, cy = by - 1 + c % 3;
+        int a = 0, b = 0;
+        if (cx >= 0 && cx < nb && cy >= 0 && cy < nb) {
+            const int col = (cx * nb + cy) * nb;
+            a = W.bin_start[col + z0];
+            b = W.bin_start[col + z1 + 1];
+        }
+        qs[c] = a;
+        pre[c + 1] = pre[c] + (b - a);
+    }
+    const int nbin = pre[9];
+    const int nset = MODE == 0 ? (skip_stale ? W.S->nstale : 0) : W.S->nhot;
+    const uint16_t* set = MODE == 0 ? W.S->stale : W.S->hot;
+    const int total_c = nbin + nset, nit = (total_c + 31) >> 5;
+    // sweep 1: count
+    int total = 0;
+    for (int it = 0; it < nit; ++it) {
+        const int t = lane + 32 * it;
+        bool hit = false;
+        if (t < total_c) {
+            int j;
+            if (t < nbin) {
+                int q = 0;
+#pragma unroll
+                for (int u = 0; u < 9; ++u)
+                    if (t >= pre[u] && t < pre[u + 1]) q = qs[u] + (t - pre[u]);
+                j = W.binned[q];
+            } else {
+                j = set[t - nbin];
+            }
+            if (j != i) {
+                const V4<R> pj = W.pos[j];
+                hit = !(MODE == 1 && t < nbin && is_active(pj)) && !(t < nbin && skip_stale && bit_of(W.sbits, j)) &&
+                      list_d2(pi, pj) < H.rlist2;
+            }
+        }
+        total += __popc(__ballot_sync(FULL, hit));
+    }
+    // storage: the shared row, or an overflow row (the slot's previous one if it had one)
+    uint16_t* out = W.nbr + (size_t)slot * REED_MAXNB;
+    const int old_m = W.nnb[slot];
+    const int old_r = old_m > NS ? (int)out[0] : -1;
+    uint16_t* dst = out;
+    int cap = NS, r = -1;
+    if (total > NS) {
+        r = old_r;
+        if (r < 0) {
+            r = REED_SPILL_ROWS;
+            if (lane == 0 && W.sp_nbr) r = atomicAdd(&W.S->nspill, 1);
+            r = __shfl_sync(FULL, r, 0);
+        }
+        if (r < REED_SPILL_ROWS && W.sp_nbr) {
+            dst = W.sp_nbr + (size_t)r * NW;
+            cap = NW;
+        }
+    }
+    __syncwarp();
+    // sweep 2: write in order, mark frozen neighbours without a row
+    int w = 0;
+    for (int it = 0; it < nit; ++it) {
+        const int t = lane + 32 * it;
+        bool hit = false;
+        int j = i;
+        V4<R> pj = pi;
+        if (t < total_c) {
+            if (t < nbin) {
+                int q = 0;
+#pragma unroll
+                for (int u = 0; u < 9; ++u)
+                    if (t >= pre[u] && t < pre[u + 1]) q = qs[u] + (t - pre[u]);
+                j = W.binned[q];
+            } else {
+                j = set[t - nbin];
+            }
+            if (j != i) {
+                pj = W.pos[j];
+                hit = !(MODE == 1 && t < nbin && is_active(pj)) && !(t < nbin && skip_stale && bit_of(W.sbits, j)) &&
+                      list_d2(pi, pj) < H.rlist2;
+            }
+        }
+        const unsigned bal = __ballot_sync(FULL, hit);
+        if (hit) {
+            const int e = w + __popc(bal & ((1u << lane) - 1u));
+            if (e < cap) dst[e] = (uint16_t)j;
+            if (!is_active(pj) && W.need_map[j] == REED_NO_SLOT) W.need_map[j] = (uint16_t)REED_PENDING;
+        }
+        w += __popc(bal);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        if (cap == NW) out[0] = (uint16_t)r;
+        if (total > cap) overflow += total - cap;
+    }
+    return min(total, cap);
 }
 
 // Block-wide exclusive prefix sums of two per-thread counts (threads own
@@ -573,6 +754,96 @@ __device__ __forceinline__ void block_scan4(TrackShared<R>* S, const int c[4], i
 // (unrolled, m <= REED_FAST_NB), or a group of 8, 16 or 32 lanes.
 __device__ __forceinline__ int centre_class(int m) { return m <= REED_FAST_NB ? 0 : (m <= 8 ? 1 : (m <= 16 ? 2 : 3)); }
 
+// Reverse entries of the slots [k0, k1) (all threads): where the centre of
+// slot k sits in the list of each integrated neighbour (lists are
+// symmetric: the same distance test from both ends), so the centre pass can
+// leave its force there.  SELECTIVE: only the rows whose slot is marked
+// (chg[slot] != 0) are recomputed.  (Four entries
+// at a time, and the neighbour's list four entries at a time, so that the
+// dependent shared-memory loads overlap.)
+template <typename R, int TT, bool SELECTIVE>
+__device__ __forceinline__ void reverse_entries(Win<R, TT>& W, int k0, int k1, int nact_slots, int& overflow,
+                                                const unsigned* chg = nullptr)
+{
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const int a = W.slot_atom[k], m = W.nnb[k];
+        if (SELECTIVE && chg[k] == 0u) continue;
+        const uint16_t* row = W.list(k, m);
+        uint8_t* rv = W.rev_row(k, m);
+        for (int q0 = 0; q0 < m; q0 += 4) {
+            unsigned sp[4];
+            int mp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sp[u] = q0 + u < m ? (unsigned)W.need_map[row[q0 + u]] : REED_NO_SLOT;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) mp[u] = sp[u] < (unsigned)nact_slots ? (int)W.nnb[sp[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (q0 + u >= m) break;
+                uint8_t e = (uint8_t)REED_NO_REV;
+                if (sp[u] < (unsigned)nact_slots) {
+                    const uint16_t* prow = W.list((int)sp[u], mp[u]);
+                    for (int t0 = 0; t0 < mp[u] && e == (uint8_t)REED_NO_REV; t0 += 4) {
+                        int pv[4];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) pv[v] = t0 + v < mp[u] ? (int)prow[t0 + v] : -1;
+#pragma unroll
+                        for (int v = 3; v >= 0; --v)
+                            if (pv[v] == a) e = (uint8_t)(t0 + v);
+                    }
+                    if (e == (uint8_t)REED_NO_REV) ++overflow;   // only with a truncated list
+                }
+                rv[q0 + u] = e;
+            }
+        }
+    }
+}
+
+// The order of the centre pass (all threads; ends with a barrier): the slots
+// class by class (see ters_centres), in slot order inside a class.
+template <typename R, int TT> __device__ void centre_order(Win<R, TT>& W, int nneed)
+{
+    TrackShared<R>* S = W.S;
+    const int kc = (nneed + blockDim.x - 1) / blockDim.x;
+    const int k0 = min(nneed, (int)threadIdx.x * kc), k1 = min(nneed, k0 + kc);
+    int c[4] = {0, 0, 0, 0}, o[4], t[4];
+    for (int k = k0; k < k1; ++k) {
+        const int cl = centre_class(W.nnb[k]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[i] += cl == i;
+    }
+    block_scan4<R>(S, c, o, t);
+    o[1] += t[0];
+    o[2] += t[0] + t[1];
+    o[3] += t[0] + t[1] + t[2];
+    for (int k = k0; k < k1; ++k) {
+        const int cl = centre_class(W.nnb[k]);
+        int dst = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (cl == i) dst = o[i]++;
+        W.order[dst] = (uint16_t)k;
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) S->ncls[i] = t[i];
+    __syncthreads();
+}
+
+// The end of a full Tersoff list build (all threads, after the lists and a
+// barrier; ends with a barrier): clears the pending marks, fills the reverse
+// entries and the order of the centre pass.
+template <typename R, int TT>
+__device__ void finish_tersoff_lists(const DevParams& P, Win<R, TT>& W, int nact_slots, int nneed, int& overflow)
+{
+    // (pending marks set by these last lists are not needed: clear them)
+    for (int i = threadIdx.x; i < P.na; i += blockDim.x)
+        if (W.need_map[i] == REED_PENDING) W.need_map[i] = (uint16_t)REED_NO_SLOT;
+    __syncthreads();
+    reverse_entries<R, TT, false>(W, 0, nneed, nact_slots, overflow);
+    centre_order<R, TT>(W, nneed);
+}
+
 template <typename R, int TT>
 __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow,
                                  int& cap_overflow, unsigned long long& spilled)
@@ -584,6 +855,11 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
     const int bchunk = (nbins + blockDim.x - 1) / blockDim.x;
     const int j0 = min(nbins, (int)threadIdx.x * bchunk), j1 = min(nbins, j0 + bchunk);
     if (threadIdx.x == 0) S->nspill = 0;
+    if constexpr (TT == REED_TT_TERSOFF) {   // every bin is current again
+        for (int w = threadIdx.x; w < (na + 31) >> 5; w += blockDim.x) W.sbits[w] = W.hbits[w] = 0u;
+        for (int k = threadIdx.x; k < P.bond_cap; k += blockDim.x) W.tmask[k] = 0u;
+        if (threadIdx.x == 0) S->nstale = S->nhot = 0;
+    }
     // bin populations and integrated atoms of this thread's chunk
     int nact = 0;
     for (int i = i0; i < i1; ++i) {
@@ -684,73 +960,228 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
         S->need_count = nneed;
         spilled += (unsigned long long)min(S->nspill, REED_SPILL_ROWS);
     }
-    // (pending marks set by these last lists are not needed: clear them)
-    for (int i = threadIdx.x; i < na; i += blockDim.x)
-        if (W.need_map[i] == REED_PENDING) W.need_map[i] = (uint16_t)REED_NO_SLOT;
-    __syncthreads();
-    // reverse entries: where the centre of slot k sits in the list of each
-    // integrated neighbour (lists are symmetric: the same distance test from
-    // both ends), so the centre pass can leave its force there
-    // (four entries at a time, and the neighbour's list four entries at a
-    // time, so that the dependent shared-memory loads overlap)
-    for (int k = threadIdx.x; k < nneed; k += blockDim.x) {
-        const int a = W.slot_atom[k], m = W.nnb[k];
-        const uint16_t* row = W.list(k, m);
-        uint8_t* rv = W.rev_row(k, m);
-        for (int q0 = 0; q0 < m; q0 += 4) {
-            unsigned sp[4];
-            int mp[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) sp[u] = q0 + u < m ? (unsigned)W.need_map[row[q0 + u]] : REED_NO_SLOT;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) mp[u] = sp[u] < (unsigned)nact_slots ? (int)W.nnb[sp[u]] : 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (q0 + u >= m) break;
-                uint8_t e = (uint8_t)REED_NO_REV;
-                if (sp[u] < (unsigned)nact_slots) {
-                    const uint16_t* prow = W.list((int)sp[u], mp[u]);
-                    for (int t0 = 0; t0 < mp[u] && e == (uint8_t)REED_NO_REV; t0 += 4) {
-                        int pv[4];
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) pv[v] = t0 + v < mp[u] ? (int)prow[t0 + v] : -1;
-#pragma unroll
-                        for (int v = 3; v >= 0; --v)
-                            if (pv[v] == a) e = (uint8_t)(t0 + v);
-                    }
-                    if (e == (uint8_t)REED_NO_REV) ++overflow;   // only with a truncated list
-                }
-                rv[q0 + u] = e;
+    finish_tersoff_lists<R, TT>(P, W, nact_slots, nneed, overflow);
+}
+
+// ---------------------------------------------------------------------------
+// Partial refresh of the Tersoff lists (no window move since the last full
+// build; all threads, after a barrier; ends with a barrier).  Only the
+// integrated atoms whose path since their last list exceeds half the skin
+// ("hot") get new lists; every other list keeps its entries, drops those of
+// hot atoms and gains the hot atoms that now list it.  A pair of atoms that
+// are both not hot has moved by at most the skin since its status was last
+// evaluated, so the lists still hold every pair within the cutoff.  The grid
+// bins are those of the last full build: atoms that have been hot since then
+// ("stale") are tested from the stale set; every other atom has moved by at
+// most half the skin, and bins at least r_list + skin/2 wide keep it in the
+// 27 bins around any point within r_list of it.  A frozen atom that becomes
+// needed gets the frozen atoms and the hot atoms within the list radius: an
+// integrated atom that is not hot cannot list it (else it would have been
+// needed already), so both ends agree.  Returns false, before changing any
+// list, when the sets or the list rows would overflow; the caller then
+// builds from scratch.
+// ---------------------------------------------------------------------------
+template <typename R, int TT>
+__device__ bool refresh_lists(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow,
+                              unsigned long long& spilled)
+{
+    const int na = P.na, tid = threadIdx.x, lane = tid & 31, nw = blockDim.x >> 5, wid = tid >> 5;
+    TrackShared<R>* S = W.S;
+    // (refreshing every atom past a quarter of the skin leaves the rest at most
+    // a quarter each, so the next refresh comes only after the two fastest have
+    // moved another half skin)
+    const R thr = R(0.25) * H.skin;
+    const int nact = S->active_count, nneed0 = S->need_count, nstale0 = S->nstale, nsp0 = S->nspill;
+    // hot atoms, among the integrated ones (slot order is atom order)
+    const int kc = (nact + blockDim.x - 1) / blockDim.x;
+    const int k0 = min(nact, tid * kc), k1 = min(nact, k0 + kc);
+    int c[4] = {0, 0, 0, 0}, o[4], t4[4];
+    for (int k = k0; k < k1; ++k) {
+        const int i = W.slot_atom[k];
+        if (W.vel[i].w > thr) {
+            ++c[0];
+            c[1] += bit_of(W.sbits, i) ? 0 : 1;
+        }
+    }
+    block_scan4<R>(S, c, o, t4);
+    const int nhot = t4[0];
+    if (nhot == 0 || nhot > REED_MAX_HOT || nstale0 + t4[1] > REED_MAX_STALE || S->nspill > REED_SPILL_ROWS / 2) {
+        __syncthreads();
+        return false;   // (overflow rows are only reclaimed by a full build)
+    }
+    {
+        int oh = o[0], os = nstale0 + o[1];
+        for (int k = k0; k < k1; ++k) {
+            const int i = W.slot_atom[k];
+            if (!(W.vel[i].w > thr)) continue;
+            S->hot[oh++] = (uint16_t)i;
+            atomicOr(&W.hbits[i >> 5], 1u << (i & 31));
+            if (!bit_of(W.sbits, i)) {
+                S->stale[os++] = (uint16_t)i;   // (atom order among the new ones)
+                atomicOr(&W.sbits[i >> 5], 1u << (i & 31));
             }
         }
     }
-    // the centre pass takes the slots class by class (see ters_centres),
-    // in slot order inside a class
-    {
-        const int kc = (nneed + blockDim.x - 1) / blockDim.x;
-        const int k0 = min(nneed, (int)threadIdx.x * kc), k1 = min(nneed, k0 + kc);
-        int c[4] = {0, 0, 0, 0}, o[4], t[4];
-        for (int k = k0; k < k1; ++k) {
-            const int cl = centre_class(W.nnb[k]);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) c[i] += cl == i;
-        }
-        block_scan4<R>(S, c, o, t);
-        o[1] += t[0];
-        o[2] += t[0] + t[1];
-        o[3] += t[0] + t[1] + t[2];
-        for (int k = k0; k < k1; ++k) {
-            const int cl = centre_class(W.nnb[k]);
-            int dst = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (cl == i) dst = o[i]++;
-            W.order[dst] = (uint16_t)k;
-        }
-        if (threadIdx.x == 0)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) S->ncls[i] = t[i];
+    __syncthreads();
+    if (tid == 0) {
+        S->nhot = nhot;
+        S->nstale = nstale0 + t4[1];
     }
+    // rows that will lose a hot atom: the old neighbours of the hot atoms
+    for (int t = wid; t < nhot; t += nw) {
+        const int kh = W.need_map[S->hot[t]], mh = W.nnb[kh];
+        const uint16_t* rh = W.list(kh, mh);
+        for (int q = lane; q < mh; q += 32) {
+            const unsigned sj = W.need_map[rh[q]];
+            if (sj < REED_PENDING) atomicOr(&W.tmask[sj], 1u << 31);
+        }
+    }
+    __syncthreads();
+    // new lists of the hot atoms (one warp each)
+    for (int t = wid; t < nhot; t += nw) {
+        const int h = S->hot[t];
+        const int k = W.need_map[h];
+        const int m = list_of_warp<R, TT, 0>(P, H, W, h, k, overflow);
+        if (lane == 0) W.nnb[k] = (uint8_t)m;
+    }
+    __syncthreads();
+    // frozen atoms that became needed must fit; nothing has changed yet
+    // that a full build would not redo
+    const int chunk = (na + blockDim.x - 1) / blockDim.x;
+    const int i0 = min(na, tid * chunk), i1 = min(na, i0 + chunk);
+    int np = 0;
+    for (int i = i0; i < i1; ++i) np += W.need_map[i] == REED_PENDING;
+    int op, dummy, tp, dummy_t;
+    block_scan2<R>(S, np, 0, op, dummy, tp, dummy_t);
+    if (nneed0 + tp > P.bond_cap) {
+        __syncthreads();
+        return false;
+    }
+    // rows that gain a hot atom: the new neighbours of the hot atoms (hot
+    // rows are rebuilt whole, rows of atoms that became needed are new)
+    for (int t = wid; t < nhot; t += nw) {
+        const int kh = W.need_map[S->hot[t]], mh = W.nnb[kh];
+        const uint16_t* rh = W.list(kh, mh);
+        for (int q = lane; q < mh; q += 32) {
+            const unsigned sj = W.need_map[rh[q]];
+            if (sj < REED_PENDING) atomicOr(&W.tmask[sj], 1u << t);
+        }
+    }
+    __syncthreads();
+    // the marked rows: drop the hot atoms, append those that list this atom
+    for (int k = tid; k < nneed0; k += blockDim.x) {
+        const unsigned mk = W.tmask[k];
+        if (!mk) continue;
+        const int a = W.slot_atom[k];
+        if (bit_of(W.hbits, a)) continue;
+        const unsigned add = mk & 0x7fffffffu;
+        const int m = W.nnb[k];
+        const uint16_t* row = W.list(k, m);
+        if (m <= maxnb(TT)) {   // in place in the shared row (entries only move down)
+            ListWriter<R, TT> L(W, k);
+            for (int q = 0; q < m; ++q) {
+                const int j = row[q];
+                if (!bit_of(W.hbits, j)) L.out[L.cnt++] = (uint16_t)j;
+            }
+            for (int t = 0; t < nhot; ++t)
+                if ((add >> t) & 1u) L.add(W, S->hot[t], overflow);
+            W.nnb[k] = (uint8_t)L.cnt;
+        } else {                // in place in the overflow row; back to the shared row if it fits
+            uint16_t* sp = const_cast<uint16_t*>(row);
+            int w = 0;
+            for (int q = 0; q < m; ++q) {
+                const int j = row[q];
+                if (!bit_of(W.hbits, j)) sp[w++] = (uint16_t)j;
+            }
+            for (int t = 0; t < nhot; ++t) {
+                if (!((add >> t) & 1u)) continue;
+                if (w < REED_SPILL_TERSOFF) sp[w++] = S->hot[t];
+                else ++overflow;
+            }
+            if (w <= maxnb(TT))
+                for (int e = 0; e < w; ++e) W.nbr[(size_t)k * REED_MAXNB + e] = sp[e];
+            W.nnb[k] = (uint8_t)w;
+        }
+    }
+    // slots of the frozen atoms that became needed, in atom order
+    op += nneed0;
+    for (int i = i0; i < i1; ++i) {
+        if (W.need_map[i] != REED_PENDING) continue;
+        W.need_map[i] = (uint16_t)op;
+        W.slot_atom[op] = (uint16_t)i;
+        W.tmask[op] = 1u << 31;   // (a new row)
+        ++op;
+    }
+    const int nneed = nneed0 + tp;
+    __syncthreads();
+    for (int k = nneed0 + wid; k < nneed; k += nw) {
+        const int i = W.slot_atom[k];
+        if (lane == 0) W.nnb[k] = 0;   // (no overflow row to reuse)
+        __syncwarp();
+        const int m = list_of_warp<R, TT, 1>(P, H, W, i, k, overflow);
+        if (lane == 0) W.nnb[k] = (uint8_t)m;
+    }
+    for (int t = tid; t < nhot; t += blockDim.x) W.tmask[W.need_map[S->hot[t]]] |= 1u << 31;   // (rebuilt rows)
+    __syncthreads();
+    if (tid == 0) {
+        S->need_count = nneed;
+        spilled += (unsigned long long)(min(S->nspill, REED_SPILL_ROWS) - min(nsp0, REED_SPILL_ROWS));
+    }
+    // (pending marks set by the new rows' lists are not needed: clear them)
+    for (int i = i0; i < i1; ++i)
+        if (W.need_map[i] == REED_PENDING) W.need_map[i] = (uint16_t)REED_NO_SLOT;
+    // reverse entries: of the changed rows, and of the rows listed in them
+    // (lists are symmetric, so those are the rows that point into them)
+    for (int k = tid; k < nneed; k += blockDim.x) {
+        if (!(W.tmask[k] & ~(1u << 30))) continue;
+        const int m = W.nnb[k];
+        const uint16_t* row = W.list(k, m);
+        for (int q = 0; q < m; ++q) {
+            const unsigned sj = W.need_map[row[q]];
+            if (sj < (unsigned)nneed) atomicOr(&W.tmask[sj], 1u << 30);
+        }
+    }
+    __syncthreads();
+    reverse_entries<R, TT, true>(W, 0, nneed, nact, overflow, W.tmask);
+    __syncthreads();
+    centre_order<R, TT>(W, nneed);
+    // the hot atoms start new paths; the marks are cleared
+    for (int k = tid; k < nneed; k += blockDim.x) W.tmask[k] = 0u;
+    for (int t = tid; t < nhot; t += blockDim.x) {
+        const int h = S->hot[t];
+        W.vel[h].w = R(0);
+        atomicAnd(&W.hbits[h >> 5], ~(1u << (h & 31)));
+    }
+    __syncthreads();
+    return true;
+}
+
+// Self-check of the Tersoff lists (option nl_check; all threads, ends with a
+// barrier): every pair of a needed atom with an atom within `r2ok` must be
+// listed, and no listed pair may be farther than r_list + skin.  Counts the
+// differences.
+template <typename R, int TT>
+__device__ void check_lists(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, R r2ok, unsigned long long& errors)
+{
+    if constexpr (TT != REED_TT_TERSOFF) return;   // (the pair lists are neighbour-major)
+    const R rmax = Mth<R>::rsqrt(H.rlist2);
+    const R lim = H.rlist2 * (R(1) + H.skin * rmax) * (R(1) + H.skin * rmax);   // (r_list + skin)^2
+    const int nneed = W.S->need_count;
+    unsigned long long e = 0;
+    for (int k = threadIdx.x; k < nneed; k += blockDim.x) {
+        const int a = W.slot_atom[k], m = W.nnb[k];
+        const uint16_t* row = W.list(k, m);
+        const V4<R> pa = W.pos[a];
+        for (int j = 0; j < P.na; ++j) {
+            if (j == a || !is_present(W.pos[j])) continue;
+            if (!(list_d2(pa, W.pos[j]) < r2ok)) continue;
+            bool found = false;
+            for (int q = 0; q < m; ++q) found = found || row[q] == j;
+            e += found ? 0 : 1;
+        }
+        for (int q = 0; q < m; ++q) e += list_d2(pa, W.pos[row[q]]) < lim ? 0 : 1;
+    }
+    errors += e;
     __syncthreads();
 }
 
@@ -1117,6 +1548,8 @@ struct WorkCount {
     unsigned long long triplets = 0;   // Tersoff bond-angle terms (one per zeta term)
     unsigned long long moved = 0;      // integrated atom updates
     unsigned long long spilled = 0;    // overflow rows taken by list builds (thread 0)
+    unsigned long long refreshes = 0;  // Tersoff partial refreshes (thread 0)
+    unsigned long long nl_errors = 0;  // list self-check differences (all threads)
 };
 
 // Force evaluation over the whole window; with KICK the second half kick is
@@ -1578,6 +2011,7 @@ __device__ void initial_forces(const DevParams& P, const HotParams<R>& H, Win<R,
         build_neighbours<R, TT>(P, H, W, nbovf, capovf, wc.spilled);
         if (threadIdx.x == 0) ++ctr_rebuild;
         __syncthreads();
+        if (P.nl_check) check_lists<R, TT>(P, H, W, H.rlist2, wc.nl_errors);
     }
     if constexpr (TT == REED_TT_TERSOFF) {
         ters_centres<R, TT>(H, W, wc.triplets);
@@ -1875,9 +2309,15 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                     m1 = fmax(m1, q1);
                 }
                 if (shift || m1 + m2 > H.skin) {
-                    build_neighbours<R, TT>(P, H, W, nbovf, capovf, wc.spilled);
+                    bool refreshed = false;
+                    if constexpr (TT == REED_TT_TERSOFF) {
+                        if (!shift) refreshed = refresh_lists<R, TT>(P, H, W, nbovf, wc.spilled);
+                    }
+                    if (!refreshed) build_neighbours<R, TT>(P, H, W, nbovf, capovf, wc.spilled);
                     __syncthreads();
-                    if (tid == 0) ++c_rebuild;
+                    if (tid == 0) ++(refreshed ? wc.refreshes : c_rebuild);
+                    if (P.nl_check)
+                        check_lists<R, TT>(P, H, W, refreshed ? H.tcut * H.tcut : H.rlist2, wc.nl_errors);
                     lap(PH_BUILD);
                 }
                 if constexpr (TT == REED_TT_TERSOFF) {
@@ -2059,6 +2499,8 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
         atomicAdd(&B.counters[C_MOVED], mv);
     }
     if (tid == 0 && wc.spilled) atomicAdd(&B.counters[C_SPILLED], wc.spilled);
+    if (tid == 0 && wc.refreshes) atomicAdd(&B.counters[C_REFRESH], wc.refreshes);
+    if (wc.nl_errors) atomicAdd(&B.counters[C_NLCHECK], wc.nl_errors);
     if (tid == 0) {
         atomicAdd(&B.counters[C_PRIMARIES], c_prim);
         atomicAdd(&B.counters[C_CLONES], c_clone);

@@ -53,7 +53,7 @@ class reed_run_opts(C.Structure):
                 ("epoch_size", C.c_int64), ("n_initial", C.c_int64), ("target_tracks", C.c_int64),
                 ("damage_n", C.c_int32), ("reserved3", C.c_int32), ("damage_voxel", C.c_double),
                 ("damage_min", C.c_double), ("adjoint", C.c_int32), ("adj_segment", C.c_int32),
-                ("adj_every", C.c_int32), ("reserved4", C.c_int32),
+                ("adj_every", C.c_int32), ("nl_check", C.c_int32),
                 ("nl_skin", C.c_double), ("de_max", C.c_double), ("pool_poll_limit", C.c_int64),
                 ("dx_min", C.c_double)]
 
@@ -84,7 +84,7 @@ class reed_stats_t(C.Structure):
         [("w_stopped", C.c_double), ("w_back", C.c_double), ("w_trunc", C.c_double), ("kernel_ms", C.c_double),
          ("threads_per_track", C.c_int32), ("ctas_per_sm", C.c_int32), ("grid", C.c_int32),
          ("smem_bytes", C.c_int32), ("splits", C.c_int64 * 16), ("pooled", C.c_int64),
-         ("nb_spilled", C.c_int64)]
+         ("nb_spilled", C.c_int64), ("list_refreshes", C.c_int64), ("nl_check_errors", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -204,7 +204,7 @@ def potentials_struct(w) -> reed_potentials:
 
 def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, record=True, record_capacity=0,
              trace_tracks=0, trace_steps=0, stream=None, adaptive=False, epoch_size=4096, n_initial=50,
-             target_tracks=0, damage=True, adjoint=False, adj_segment=200, adj_every=20, nl_skin=0.0,
+             target_tracks=0, damage=True, adjoint=False, adj_segment=200, adj_every=20, nl_skin=0.0, nl_check=False,
              device_thresholds=False, thresholds=None, pool_poll_limit=0) -> reed_run_opts:
     o = reed_run_opts()
     o.dt_max_fs, o.dx_max, o.e_stop = w["dt_max_fs"], w["dx_max"], w["e_stop"]
@@ -229,6 +229,7 @@ def run_opts(w, precision=PREC_MIXED, first_id=0, threads=0, ctas_per_sm=0, reco
     o.damage_voxel, o.damage_min = float(w.get("damage_voxel", 10.0)), float(w.get("damage_min", 0.1))
     o.adjoint, o.adj_segment, o.adj_every = (1 if adjoint else 0), adj_segment, adj_every
     o.nl_skin = nl_skin
+    o.nl_check = 1 if nl_check else 0
     o.de_max = float(w.get("de_max", 0.0))
     o.dx_min = float(w.get("dx_min", 0.0))
     o.pool_poll_limit = pool_poll_limit

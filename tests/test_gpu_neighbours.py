@@ -90,3 +90,21 @@ def test_lists_beyond_the_overflow_rows_are_refused(R, O):
         # the context stays usable
         Xc, Sc = _cluster(5.431, 1, np.zeros(3))
         ctx.forces(np.array([30.0, 30.0, 30.0]), Xc, Sc, precision=0)
+
+
+@pytest.mark.parametrize("prec,n", [(0, 96), (1, 24)])
+def test_refreshed_lists_stay_exact(R, prec, n):
+    """Whole As 10 keV Tersoff tracks with the lists' self-check on: after
+    every full build, each list equals a brute-force search of the window;
+    after every partial refresh (only the lists of atoms that moved more
+    than half the skin recomputed), every pair within the Tersoff cutoff is
+    listed and no listed pair is farther than the list radius plus the skin.
+    Rebuilds at window moves and refreshes between them both happen."""
+    w = workload("as10kev_si_300k_tersoff")
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n, seed=3, precision=prec, nl_check=True)
+        st = ctx.stats()
+    assert st["tracks"] == n and st["failed"] == 0
+    assert st["rebuilds"] > 0 and st["list_refreshes"] > 0, st
+    assert st["nl_check_errors"] == 0, st
+    assert st["nb_overflow"] == 0 and st["bond_cap_overflow"] == 0

@@ -1670,6 +1670,23 @@ __device__ void force_phase(const DevParams& P, const HotParams<R>& H, Win<R, TT
         for (int i = threadIdx.x; i < P.na; i += blockDim.x) {
             const V4<R> p = W.pos[i];
             if (!is_present(p)) continue;
+            if (KICK && !is_active(p)) {
+                // a frozen atom during a step: only its pair with the ion
+                // matters (its own force is never used)
+                const R dx = p.x - W.S->rel[0], dy = p.y - W.S->rel[1], dz = p.z - W.S->rel[2];
+                const R r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < H.rc2) {
+                    R U, rw;
+                    const R g = ion_pair<R>(H, P.spline_on, P.rho_on, species_of(p), r2, U, rw);
+                    out.fx += g * dx;
+                    out.fy += g * dy;
+                    out.fz += g * dz;
+                    out.rho += rw;
+                    out.epot += U;
+                    out.pairs += 1;
+                }
+                continue;
+            }
             const unsigned sl = W.need_map[i];
             if (is_active(p) && sl < (unsigned)nact) continue;   // done above
             const int k = (sl < REED_PENDING && want_energy) ? (int)sl : -1;
@@ -2258,8 +2275,11 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
             // moves in this step)
             R pm1 = R(0), pm2 = R(0);   // this thread's two longest paths
             for (int i = tid; i < P.na; i += blockDim.x) {
-                V4<R> p = W.pos[i], v = W.vel[i], f = W.frc[i];
-                if (is_active(p)) {
+                V4<R> p = W.pos[i];
+                const bool act = is_active(p);
+                if (!act && !shift) continue;   // frozen atoms do not move
+                V4<R> v = W.vel[i], f = W.frc[i];
+                if (act) {
                     ++wc.moved;
                     const R k = hdt * H.invM2[species_of(p)];
                     v.x += k * f.x;

@@ -71,18 +71,24 @@ def test_short_track_sensitivities_match_oracle(R, O, prec, seg, every, theta):
     stopped = np.nonzero(rec["status"] == STOPPED)[0]
     assert len(stopped) >= n // 2
     refs = _oracle_tangents(O, p, 0, rec["primary"][stopped], seg, every)
-    ztol, gtol = (1e-7, 1e-6) if prec == 1 else (1e-3, 2e-2)
-    compared = 0
+    # per parameter, relative to the oracle's tangent (components below 1e-3
+    # of the track's largest are held to that floor): FP64 1e-6; the mixed
+    # form 1e-3 (measured: at most 9.5e-4 over 48 tracks of each case)
+    ztol, gtol = (1e-7, 1e-6) if prec == 1 else (1e-3, 1e-3)
+    compared, worst = 0, 0.0
     for i, ref in zip(stopped, refs):
         assert ref is not None
         if prec == 0 and (ref["T"] != rec["steps"][i] or abs(ref["z"] - rec["z"][i]) > ztol):
-            continue   # FP32 forces: an occasional trajectory parts from the FP64 one
+            continue   # FP32 forces: a trajectory may part from the FP64 one
         assert ref["T"] == rec["steps"][i] and abs(ref["z"] - rec["z"][i]) <= ztol, (i, ref, rec[i])
         compared += 1
         scale = np.maximum(np.abs(ref["grad"]), 1e-3 * np.max(np.abs(ref["grad"])))
         err = np.max(np.abs(g[i] - ref["grad"]) / scale)
+        worst = max(worst, err)
         assert err <= gtol, (i, g[i], ref["grad"], err)
-    assert compared >= (len(stopped) if prec == 1 else 3 * len(stopped) // 4)
+    # at most one track in eight may part from the oracle's trajectory
+    assert compared >= (len(stopped) if prec == 1 else len(stopped) - len(stopped) // 8), (compared, len(stopped))
+    print("compared %d of %d stopped tracks, worst relative error %.2e" % (compared, len(stopped), worst))
 
 
 @pytest.mark.parametrize("prec", [0, 1])

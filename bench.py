@@ -402,7 +402,8 @@ def main():
             "e2e": e2e,
             "stats": {k: st[k] for k in ("primaries", "tracks", "steps", "pair_evals", "bond_evals", "triplets",
                                          "atom_updates", "shifts", "rebuilds", "list_refreshes", "nb_overflow", "bond_cap_overflow", "nb_spilled",
-                                         "threads_per_track", "ctas_per_sm", "grid", "smem_bytes", "phase_cycles")},
+                                         "threads_per_track", "ctas_per_sm", "grid", "smem_bytes", "phase_cycles",
+                                         "centre_class")},
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -190,9 +190,9 @@ typedef struct {
     /* Target neighbour lists (Tersoff, Buckingham): list radius = cutoff +
      * nl_skin; the lists are rebuilt after a window move and when the two
      * longest atom paths since their last list add up to more than nl_skin
-     * (Tersoff: then only the lists of atoms whose path exceeds nl_skin / 2
+     * (Tersoff: then only the lists of atoms whose path exceeds nl_skin / 4
      * are recomputed, and the entries of the others that involve them).
-     * 0 = 0.2 A for Tersoff, 0.3 A for the pair lists. */
+     * 0 = 0.3 A for Tersoff and for the pair lists. */
     double nl_skin;
     /* Energy term of the adaptive step (the paper's step rule in terms of the
      * kinetic and collisional energy, Sec. 2): when > 0, also
@@ -248,9 +248,12 @@ typedef struct {
     int64_t nb_spilled;      /* lists that outgrew their shared-memory row and moved whole
                                 to an overflow row in global memory (exact, only slower) */
     int64_t list_refreshes;  /* Tersoff partial list refreshes (only the lists of atoms that
-                                moved more than half the skin recomputed) */
+                                moved more than a quarter of the skin recomputed) */
     int64_t nl_check_errors; /* with opt->nl_check: list entries that differ from a
                                 brute-force search (0 when the lists are exact) */
+    int64_t centre_class[4]; /* Tersoff centre evaluations per step, summed over steps, by
+                                list length: at most 4 neighbours (one thread per centre),
+                                5-8, 9-16 and more (8, 16 or 32 lanes per centre) */
 } reed_stats_t;
 
 typedef struct reed_ctx reed_ctx;

@@ -37,9 +37,10 @@ const double kFluorite[12][3] = {{0, 0, 0},       {0, .5, .5},     {.5, 0, .5}, 
 // ZBL-correction knot radii (A); B-splines are centred on ln r of each.
 const double kKnots[6] = {0.2, 0.35, 0.6, 1.0, 1.7, 3.0};
 
-// default neighbour-list skins, A (measured: the Tersoff bench runs 4-5 %
-// faster at 0.2 than at 0.3, the CeO2 pair lists are best at 0.3)
-const double kSkinTersoff = 0.2;
+// default neighbour-list skins, A (measured on the As 10 keV Tersoff batch
+// with partial refreshes: 0.2 / 0.25 / 0.3 A give 15.7 / 16.3 / 16.3 M
+// ion-steps/s; the CeO2 pair lists are best at 0.3)
+const double kSkinTersoff = 0.3;
 const double kSkinPairs = 0.3;
 #define REED_NTHETA_HOST 8
 #define REED_STEP_RING_HOST 256
@@ -967,6 +968,7 @@ int reed_stats(reed_ctx* ctx, reed_stats_t* out)
     out->triplets = (int64_t)c[C_TRIPLETS];
     out->atom_updates = (int64_t)c[C_MOVED];
     for (int k = 0; k < REED_NPHASE; ++k) out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
+    for (int k = 0; k < 4; ++k) out->centre_class[k] = (int64_t)c[C_CLS0 + k];
     for (int k = 0; k < REED_MAX_THR; ++k) out->splits[k] = (int64_t)sp[k];
     out->pooled = (int64_t)sp[REED_MAX_THR];
     out->failed = (int64_t)c[C_FAILED];
@@ -1677,6 +1679,7 @@ extern "C" int reed_run_static(const reed_lattice* lat, const reed_species* sp, 
         stats_out->triplets = (int64_t)c[C_TRIPLETS];
         stats_out->atom_updates = (int64_t)c[C_MOVED];
         for (int k = 0; k < REED_NPHASE; ++k) stats_out->phase_cycles[k] = (int64_t)c[C_PHASE0 + k];
+        for (int k = 0; k < 4; ++k) stats_out->centre_class[k] = (int64_t)c[C_CLS0 + k];
         unsigned long long sp[REED_MAX_THR + 1];
         CK(cudaMemcpy(sp, B.splits, sizeof(sp), cudaMemcpyDeviceToHost));
         for (int k = 0; k < REED_MAX_THR; ++k) stats_out->splits[k] = (int64_t)sp[k];

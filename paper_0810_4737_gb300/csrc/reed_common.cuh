@@ -43,7 +43,7 @@ __host__ __device__ constexpr int spill_width(int tt)
 //   -1 for an empty slot (cell above the surface).
 #define REED_W_EMPTY (-1)
 
-enum { REED_NCOUNT = 27 };
+enum { REED_NCOUNT = 30 };
 enum { REED_NRED = 9 };   // per-warp partial sums of a force pass
 // cycle counters of the step phases (thread 0 of every CTA, summed)
 enum { PH_ION = 0, PH_MOVE, PH_BUILD, PH_PASS1, PH_FORCE, PH_ADMIN, REED_NPHASE };
@@ -52,7 +52,10 @@ enum {
     C_PRIMARIES = 0, C_CLONES, C_TRACKS, C_STEPS, C_PAIRS, C_BONDS, C_SHIFTS, C_REBUILDS,
     C_DROPPED, C_NBOVF, C_FAILED, C_STOP, C_BACK, C_TRUNC, C_CAPOVF, C_TRIPLETS, C_MOVED, C_SPILLED, C_REFRESH,
     C_NLCHECK, C_SPARE
-};   // C_SPARE .. C_SPARE + REED_NPHASE - 1 hold the phase clocks
+};   // C_SPARE .. C_SPARE + REED_NPHASE - 1 hold the phase clocks, then C_CLS0 ..
+     // C_CLS0 + 3 the Tersoff centre evaluations by class
+#define C_CLS0 (C_SPARE + REED_NPHASE)
+static_assert(C_CLS0 + 4 == REED_NCOUNT, "counter layout");
 enum { W_STOPPED = 0, W_BACK, W_TRUNC, W_FAILED };
 
 // Hot-loop parameters in the arithmetic type of the force pass (float for

@@ -70,6 +70,7 @@ template <typename R> struct TrackShared {
     int need_count, active_count;
     int nspill;           // overflow rows taken by the current lists
     int ncls[4];          // Tersoff: slots per centre-pass class, in `order` (see ters_centres)
+    unsigned long long cls_sum[4];   // centre evaluations per class, summed over passes (thread 0)
     // Tersoff partial refreshes: atoms whose bins are stale since the last
     // full build (atom order), and the atoms refreshed now
     int nstale, nhot;
@@ -966,20 +967,20 @@ __device__ void build_neighbours(const DevParams& P, const HotParams<R>& H, Win<
 // ---------------------------------------------------------------------------
 // Partial refresh of the Tersoff lists (no window move since the last full
 // build; all threads, after a barrier; ends with a barrier).  Only the
-// integrated atoms whose path since their last list exceeds half the skin
-// ("hot") get new lists; every other list keeps its entries, drops those of
-// hot atoms and gains the hot atoms that now list it.  A pair of atoms that
-// are both not hot has moved by at most the skin since its status was last
-// evaluated, so the lists still hold every pair within the cutoff.  The grid
-// bins are those of the last full build: atoms that have been hot since then
-// ("stale") are tested from the stale set; every other atom has moved by at
-// most half the skin, and bins at least r_list + skin/2 wide keep it in the
-// 27 bins around any point within r_list of it.  A frozen atom that becomes
-// needed gets the frozen atoms and the hot atoms within the list radius: an
-// integrated atom that is not hot cannot list it (else it would have been
-// needed already), so both ends agree.  Returns false, before changing any
-// list, when the sets or the list rows would overflow; the caller then
-// builds from scratch.
+// integrated atoms whose path since their last list exceeds a quarter of the
+// skin ("hot") get new lists; every other list keeps its entries, drops those
+// of hot atoms and gains the hot atoms that now list it.  A pair of atoms
+// that are both not hot has moved by at most half the skin since its status
+// was last evaluated, so the lists still hold every pair within the cutoff.
+// The grid bins are those of the last full build: atoms that have been hot
+// since then ("stale") are tested from the stale set; every other atom has
+// moved by at most a quarter of the skin, and bins at least r_list + skin/2
+// wide keep it in the 27 bins around any point within r_list of it.  A
+// frozen atom that becomes needed gets the frozen atoms and the hot atoms
+// within the list radius: an integrated atom that is not hot cannot list it
+// (else it would have been needed already), so both ends agree.  Returns
+// false, before changing any list, when the sets or the list rows would
+// overflow; the caller then builds from scratch.
 // ---------------------------------------------------------------------------
 template <typename R, int TT>
 __device__ bool refresh_lists(const DevParams& P, const HotParams<R>& H, Win<R, TT>& W, int& overflow,
@@ -2099,7 +2100,10 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
             t_mark = now;
         }
     };
-    if (tid == 0) S->top = 0;
+    if (tid == 0) {
+        S->top = 0;
+        for (int c = 0; c < 4; ++c) S->cls_sum[c] = 0;
+    }
     W.clear_grid(P);
 
     for (;;) {
@@ -2344,6 +2348,8 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
                     ters_centres<R, TT>(H, W, wc.triplets);
                     __syncthreads();
                     lap(PH_PASS1);
+                    if (tid == 0)
+                        for (int c = 0; c < 4; ++c) S->cls_sum[c] += (unsigned)S->ncls[c];
                 }
             }
             force_phase<R, TT, true>(P, H, W, hdt, q, false);
@@ -2520,6 +2526,9 @@ __global__ void __launch_bounds__((track_max_threads<TT>()), (track_min_ctas<R, 
     }
     if (tid == 0 && wc.spilled) atomicAdd(&B.counters[C_SPILLED], wc.spilled);
     if (tid == 0 && wc.refreshes) atomicAdd(&B.counters[C_REFRESH], wc.refreshes);
+    if (TT == REED_TT_TERSOFF && tid == 0)
+        for (int c = 0; c < 4; ++c)
+            if (S->cls_sum[c]) atomicAdd(&B.counters[C_CLS0 + c], S->cls_sum[c]);
     if (wc.nl_errors) atomicAdd(&B.counters[C_NLCHECK], wc.nl_errors);
     if (tid == 0) {
         atomicAdd(&B.counters[C_PRIMARIES], c_prim);

@@ -84,11 +84,13 @@ class reed_stats_t(C.Structure):
         [("w_stopped", C.c_double), ("w_back", C.c_double), ("w_trunc", C.c_double), ("kernel_ms", C.c_double),
          ("threads_per_track", C.c_int32), ("ctas_per_sm", C.c_int32), ("grid", C.c_int32),
          ("smem_bytes", C.c_int32), ("splits", C.c_int64 * 16), ("pooled", C.c_int64),
-         ("nb_spilled", C.c_int64), ("list_refreshes", C.c_int64), ("nl_check_errors", C.c_int64)]
+         ("nb_spilled", C.c_int64), ("list_refreshes", C.c_int64), ("nl_check_errors", C.c_int64),
+         ("centre_class", C.c_int64 * 4)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["phase_cycles"] = list(self.phase_cycles)
+        d["centre_class"] = list(self.centre_class)
         d["splits"] = list(self.splits)
         return d
 

@@ -7,13 +7,13 @@ at which the FP64 CPU oracle stopped it (Sec. 2, the range density).  It calls
 only ``oracle/`` and reads its inputs from the workload definitions; nothing
 here comes from the CUDA path.
 
-    python tests/golden/make_range_goldens.py --workload as10kev_si_300k_tersoff --n 4096
+    python tests/golden/make_range_goldens.py --workload as10kev_si_300k_tersoff --n 8192
     python tests/golden/make_range_goldens.py --workload ar30kev_ceo2_300k_buck --n 2048
     python tests/golden/make_range_goldens.py --workload kr85mev_uo2_300k_recoil --n 256
 
 Rows are appended chunk by chunk, so an interrupted run resumes where it
-stopped.  Cloning depths are switched off: every primary is one unweighted
-track.
+stopped, and a larger --n extends a file.  Cloning depths are switched off:
+every primary is one unweighted track.
 """
 from __future__ import annotations
 
@@ -61,14 +61,20 @@ def main():
     w = workload(a.workload, thresholds=[])
     p = O.params(w)
     out = path_for(a.workload)
+    header = [f"# oracle range records of {a.workload}, primaries 0..{a.n - 1}, seed {SEED}, no cloning\n",
+              f"# written by: python tests/golden/make_range_goldens.py --workload {a.workload} --n {a.n}\n",
+              "# id  depth_A  status(1 stopped, 2 backscattered, 3 truncated)  steps\n"]
     done = 0
     if os.path.exists(out):
         done = len(read(a.workload)[0])
+        # (more primaries than the file holds: the rows stay, the header names the new count)
+        with open(out) as f:
+            rows = [line for line in f if not line.startswith("#")]
+        with open(out, "w") as f:
+            f.writelines(header + rows)
     else:
         with open(out, "w") as f:
-            f.write(f"# oracle range records of {a.workload}, primaries 0..{a.n - 1}, seed {SEED}, no cloning\n")
-            f.write(f"# written by: python tests/golden/make_range_goldens.py --workload {a.workload} --n {a.n}\n")
-            f.write("# id  depth_A  status(1 stopped, 2 backscattered, 3 truncated)  steps\n")
+            f.writelines(header)
     t0 = time.time()
     while done < a.n:
         m = min(a.chunk, a.n - done)

@@ -1,0 +1,107 @@
+"""Range profiles of the benchmarked configurations against the oracle.
+
+The range density (Sec. 2) is what REED-MD computes; its per-track
+trajectories are chaotic beyond a few hundred steps, so parity is
+statistical: the projected-range distribution of GPU tracks against the
+FP64 oracle's, on independent samples of the same workload (GPU seed 1,
+oracle seed 0).  The oracle's ranges are stored in tests/golden/ by
+make_range_goldens.py, which calls only oracle/.
+
+Tolerances: mean and straggle within 2 %, or within three combined
+sampling errors when those are larger (the error of each relative
+difference is stated in the assertion message); two-sample KS p > 0.01;
+backscattered fraction within four binomial errors.  Each test also checks
+that it has the power to see a shift of the mean: the same comparison on the
+GPU ranges scaled by 1 + shift must fail (3 % for the Kr fragments; 4 % for
+As in Si, whose straggle is 60 % of the mean range, so that 4096 oracle
+tracks leave a 1 % sampling error on the mean).
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_0810_4737_gb300.workloads import workload
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "golden"))
+import make_range_goldens as G  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_0810_4737_gb300 import build, reed
+    build.build()
+    return reed
+
+
+def _se_mean(z):
+    return np.std(z) / np.sqrt(len(z)) / np.mean(z)
+
+
+def _se_std(z):
+    # relative standard error of a sample standard deviation: sqrt((kurtosis - 1) / (4 n))
+    d = z - np.mean(z)
+    return np.sqrt(max(np.mean(d ** 4) / np.mean(d ** 2) ** 2 - 1.0, 0.0) / (4 * len(z)))
+
+
+def compare(zg, zo):
+    """Relative differences of mean and straggle with their sampling errors,
+    the tolerance each is held to, and the KS p-value."""
+    dm = np.mean(zg) / np.mean(zo) - 1.0
+    ds = np.std(zg) / np.std(zo) - 1.0
+    sm = float(np.hypot(_se_mean(zg), _se_mean(zo)))
+    ss = float(np.hypot(_se_std(zg), _se_std(zo)))
+    return {"mean_rel": dm, "mean_se": sm, "mean_tol": max(0.02, 3 * sm),
+            "straggle_rel": ds, "straggle_se": ss, "straggle_tol": max(0.02, 3 * ss),
+            "ks_p": float(stats.ks_2samp(zg, zo).pvalue)}
+
+
+def passes(c):
+    return abs(c["mean_rel"]) <= c["mean_tol"] and abs(c["straggle_rel"]) <= c["straggle_tol"] and c["ks_p"] > 0.01
+
+
+def _golden(name):
+    ids, z, st, steps = G.read(name)
+    return np.asarray(z), np.asarray(st)
+
+
+def _check(R, name, n_gpu, prec, shift=0.03, **kw):
+    zo_all, so = _golden(name)
+    w = workload(name, thresholds=[])
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=n_gpu, seed=1, precision=prec, **kw)
+        rec = ctx.records()
+        st = ctx.stats()
+    assert st["tracks"] == n_gpu and st["nb_overflow"] == 0 and st["bond_cap_overflow"] == 0
+    assert st["truncated"] == 0 and np.sum(so == 3) == 0
+    zg, zo = rec["z"][rec["status"] == 1], zo_all[so == 1]
+    c = compare(zg, zo)
+    assert passes(c), c
+    # power: a mean range longer by `shift` is caught
+    assert not passes(compare((1.0 + shift) * zg, zo)), compare((1.0 + shift) * zg, zo)
+    # backscattered fraction within four binomial errors
+    fo, fg = np.mean(so == 2), np.mean(rec["status"] == 2)
+    sig = np.sqrt(fo * (1 - fo) / len(so) + fg * (1 - fg) / n_gpu)
+    assert abs(fg - fo) <= 4 * sig + 1e-12, (fg, fo, sig)
+    print(name, "precision", prec, {k: round(float(v), 4) for k, v in c.items()})
+    return c
+
+
+@pytest.mark.parametrize("prec,n", [(0, 32768), (1, 16384)])
+def test_as10kev_tersoff_ranges_match_oracle(R, prec, n):
+    """The oracle tracks of the benchmarked workload (As 10 keV into Si at
+    300 K, Tersoff target, 5^3-cell window) against 32768 GPU tracks in the
+    mixed form and 16384 in FP64."""
+    _check(R, "as10kev_si_300k_tersoff", n, prec, shift=0.04)
+
+
+def test_kr_fission_fragment_ranges_match_oracle(R):
+    """256 oracle tracks of 85 MeV Kr fission fragments in bulk UO2 (Sec.
+    4.2; the energy term of the step and its floor), against 1024 GPU tracks
+    in the mixed form (the FP64 path would take minutes per track batch)."""
+    _check(R, "kr85mev_uo2_300k_recoil", 1024, 0)

@@ -41,10 +41,10 @@ OPS_PAIR, OPS_MOVE, OPS_TRIPLET = 35, 24, 60
 SFU_PAIR, SFU_TRIPLET = 5, 1
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of one bench launch of the stepper kernel (4096
-# ions), from the one-pass ncu capture of that launch summarised in
-# profiles/reed_track_kernel_tersoff_as10kev.md (None when the kernel has
-# changed since).
-TRAFFIC_PER_LAUNCH = None
+# ions), from the one-pass ncu capture of that launch (dram__bytes_read.sum
+# 680,192 B + dram__bytes_write.sum 0 B; the Tersoff summary under profiles/
+# gives the command).  None once the kernel changes.
+TRAFFIC_PER_LAUNCH = 680192
 
 
 def _ion_name(w):

@@ -505,10 +505,10 @@ int reed_window_replay(reed_ctx* ctx, int precision, uint64_t key, const double*
  * array of 64 MiB that every GPU loading the library holds until the process
  * exits.  The array's device address belongs to a CUDA context: the first
  * call in each context of a device looks it up (cudaGetSymbolAddress) and
- * caches it under the context's unique id, so make that first call before
- * any stream capture.  Configurations whose scratch does not fit (SMs x
- * (n_thresholds x window record + overflow rows)) are rejected with
- * REED_E_ARG; the launch uses fewer CTAs per SM when that makes it fit.  No
+ * caches it under the context's unique id.  Configurations whose scratch
+ * does not fit (SMs x (n_thresholds x window record + overflow rows)) are
+ * rejected with REED_E_ARG; the launch uses fewer CTAs per SM when that
+ * makes it fit.  No
  * per-track records or traces (record_tracks, trace_tracks, trace_steps
  * must be 0).
  *

@@ -12,9 +12,16 @@ sampling errors when those are larger (the error of each relative
 difference is stated in the assertion message); two-sample KS p > 0.01;
 backscattered fraction within four binomial errors.  Each test also checks
 that it has the power to see a shift of the mean: the same comparison on the
-GPU ranges scaled by 1 + shift must fail (3 % for the Kr fragments; 4 % for
-As in Si, whose straggle is 60 % of the mean range, so that 4096 oracle
-tracks leave a 1 % sampling error on the mean).
+GPU ranges scaled by 1 + shift must fail, with the smallest shift the
+samples resolve: 3 % for the Kr fragments; 4 % for As in Si, whose straggle
+is 60 % of the mean range (4096 oracle tracks leave 1 % of sampling error on
+the mean); 7 % for Ar in CeO2 (straggle 80 % of the mean, 2048 oracle
+tracks).
+
+A second comparison runs the oracle's own primaries on the GPU (the same
+launch draws) and tests the paired differences of the ranges, which resolve
+the mean to a fraction of a percent: FP64 within max(0.5 %, 3 se) and
+mixed within max(2 %, 3 se), with the per-primary correlation stated.
 """
 import os
 import sys
@@ -98,6 +105,56 @@ def test_as10kev_tersoff_ranges_match_oracle(R, prec, n):
     300 K, Tersoff target, 5^3-cell window) against 32768 GPU tracks in the
     mixed form and 16384 in FP64."""
     _check(R, "as10kev_si_300k_tersoff", n, prec, shift=0.04)
+
+
+def test_ceo2_buckingham_ranges_match_oracle(R):
+    """2048 oracle tracks of Ar 30 keV into CeO2 (fluorite, Buckingham pairs
+    with a ZBL core, directions within 10 deg of [001]) against 16384 GPU
+    tracks in the mixed form (FP64: the paired test below).  The straggle is
+    80 % of the mean range (channelled tracks), so the oracle sample alone
+    leaves 1.8 % of sampling error on the mean: the power check uses the 7 %
+    shift these samples resolve."""
+    _check(R, "ar30kev_ceo2_300k_buck", 16384, 0, shift=0.07)
+
+
+# FP64: the paired mean within max(0.5 %, 3 se) and a track-by-track
+# correlation above 0.9 (measured: As +6e-7 +- 6e-6 with r = 0.9999997,
+# CeO2 +0.3 % +- 0.5 % with r = 0.965); mixed form: within max(2 %, 3 se)
+# and r > 0.7 (measured: As -0.56 % +- 0.23 %, r = 0.96; CeO2 +1.1 % +- 1.2 %,
+# r = 0.78).
+PAIRED_TOL = {0: (0.02, 0.7), 1: (0.005, 0.9)}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["as10kev_si_300k_tersoff", "ar30kev_ceo2_300k_buck"])
+def test_ranges_match_oracle_on_the_same_primaries(R, name, prec):
+    """The oracle's own primaries (seed 0, ids 0..n-1) on the GPU.  Launch
+    position and direction are drawn from the same counter-based streams,
+    so each primary starts identically; trajectories part only as rounding
+    is amplified collision by collision, and per-primary ranges stay
+    correlated.  The paired difference z_gpu - z_oracle then resolves the
+    mean range far more finely than two independent samples."""
+    ids, zo, so, _ = (np.asarray(a) for a in G.read(name))
+    w = workload(name, thresholds=[])
+    with R.Reed(w) as ctx:
+        ctx.run(n_ions=len(ids), seed=0, precision=prec)
+        rec = ctx.records()
+    rec = rec[np.argsort(rec["id"])]
+    assert np.array_equal(rec["id"], ids)
+    zg, sg = rec["z"], rec["status"]
+    both = (sg == 1) & (so == 1)
+    assert both.sum() >= 0.9 * len(ids)
+    d = zg[both] - zo[both]
+    m = zo[both].mean()
+    rel, se = d.mean() / m, d.std(ddof=1) / np.sqrt(len(d)) / m
+    r = float(np.corrcoef(zg[both], zo[both])[0, 1])
+    tol, rmin = PAIRED_TOL[prec]
+    print(name, "precision", prec, "paired mean %+.2e +- %.1e, r = %.7f" % (rel, se, r))
+    assert abs(rel) <= max(tol, 3 * se), (rel, se)
+    assert r > rmin, r
+    # the status of each primary: backscattered in one and stopped in the
+    # other happens only where the trajectories have parted
+    assert np.mean(sg != so) < 0.10
 
 
 def test_kr_fission_fragment_ranges_match_oracle(R):

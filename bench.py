@@ -146,30 +146,48 @@ def cpu_baseline(w, n_ions, threads, step_cap):
     return r["steps"] / dt, r["steps"], dt
 
 
+def _golden():
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_range_goldens as G
+    return G
+
+
 def oracle_parity(w, forms):
     """Mean, straggle and two-sample KS p of the range profile of each GPU
     form against the oracle's ranges of the same workload, stored by
-    tests/golden/make_range_goldens.py (independent primaries: GPU and oracle
-    samples use different seeds).  forms: {name: (depths of stopped tracks, n)}."""
-    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    tests/golden/make_range_goldens.py, and the paired comparison on the
+    primaries both sides ran (the GPU forms run the oracle's primaries: the
+    same seed and ids, so the same launch draws).  forms: {name: records}."""
     try:
-        import make_range_goldens as G
+        G = _golden()
         ids, z, st, _ = G.read(w["name"])
     except (ImportError, OSError) as e:
         return {"workload": w["name"], "unavailable": "no stored oracle ranges (%s)" % e}
-    z, st = np.asarray(z), np.asarray(st)
+    ids, z, st = np.asarray(ids), np.asarray(z), np.asarray(st)
     zo = z[st == 1]
     out = {"workload": w["name"], "oracle_ions": len(ids), "oracle_mean_A": float(np.mean(zo)),
            "oracle_straggle_A": float(np.std(zo)), "source": "tests/golden/ranges_%s.txt (FP64 C oracle)" % w["name"]}
-    for name, (zg, n) in forms.items():
+    for name, rec in forms.items():
+        zg = rec["z"][rec["status"] == 1]
         if len(zg) < 2:
             continue
-        out[name] = {"ions": n, "mean_rel_err": float(np.mean(zg) / np.mean(zo) - 1),
-                     "straggle_rel_err": float(np.std(zg) / np.std(zo) - 1), "ks_p": _ks(zg, zo),
-                     # sampling error of the two estimates (trajectories are chaotic, so
-                     # the two samples are effectively independent)
-                     "mean_rel_se": float(np.hypot(_se_mean(zg), _se_mean(zo))),
-                     "straggle_rel_se": float(np.hypot(_se_std(zg), _se_std(zo)))}
+        res = {"ions": len(rec), "mean_rel_err": float(np.mean(zg) / np.mean(zo) - 1),
+               "straggle_rel_err": float(np.std(zg) / np.std(zo) - 1), "ks_p": _ks(zg, zo),
+               # sampling errors as for independent samples (an upper bound here)
+               "mean_rel_se": float(np.hypot(_se_mean(zg), _se_mean(zo))),
+               "straggle_rel_se": float(np.hypot(_se_std(zg), _se_std(zo)))}
+        # paired: the same primary on both sides, both stopped
+        r = rec[np.argsort(rec["id"])]
+        k = r["id"] < len(ids)
+        r = r[k]
+        both = (r["status"] == 1) & (st[r["id"]] == 1)
+        if both.sum() > 2:
+            a, b = r["z"][both], z[r["id"][both]]
+            d = a - b
+            res["paired"] = {"primaries": int(both.sum()), "mean_rel_err": float(d.mean() / b.mean()),
+                             "mean_rel_se": float(d.std(ddof=1) / np.sqrt(len(d)) / b.mean()),
+                             "correlation": float(np.corrcoef(a, b)[0, 1])}
+        out[name] = res
     return out
 
 
@@ -327,29 +345,33 @@ def main():
         d2h = 8 * (nb + 3) + ctypes.sizeof(R.reed_stats_t)
         e2e = {"value": e2e_steps / dt, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "note": "reed_run + reed_range_profile (into pinned host memory) + reed_stats per step, host wall clock"}
-    # ---- the plain FP64 path on the batch of the first timed step (the same
-    # primaries as that step's mixed-form run), and the KS check of the two profiles
+    # ---- the plain FP64 path on a full batch, and the mixed form on the same
+    # primaries: the oracle's stored ones (its seed, ids 0..m-1), so that both
+    # profiles can also be paired with the oracle's track by track
     fp64, forms = None, {}
     m = n if args.fp64_ions < 0 else args.fp64_ions
     if rank == 0 and m > 0:
-        fid = first + args.warmup * n   # the first timed step's primaries
+        try:
+            pseed = _golden().SEED
+        except ImportError:
+            pseed = w["seed"]
         with R.Reed(w) as c64, R.Reed(w) as c32:
             # (the FP64 path runs in the library's default launch shape)
-            c64.run(n_ions=m, seed=w["seed"], first_id=fid, precision=R.PREC_FP64, stream=sh)
+            c64.run(n_ions=m, seed=pseed, first_id=0, precision=R.PREC_FP64, stream=sh)
             s64 = c64.stats()
             r64 = c64.records()
-            c32.run(n_ions=m, seed=w["seed"], first_id=fid, precision=R.PREC_MIXED, stream=sh, **launch)
+            c32.run(n_ions=m, seed=pseed, first_id=0, precision=R.PREC_MIXED, stream=sh, **launch)
             s32 = c32.stats()
             r32 = c32.records()
         z64 = r64["z"][r64["status"] == R.STOPPED]
         z32 = r32["z"][r32["status"] == R.STOPPED]
-        forms = {"mixed": (z32, m), "fp64": (z64, m)}
+        forms = {"mixed": r32, "fp64": r64}
         f64ops = OPS_PAIR * s64["pair_evals"] + OPS_MOVE * s64["atom_updates"] + OPS_TRIPLET * s64["triplets"]
         a64 = f64ops / (s64["kernel_ms"] * 1e-3) / 1e12
         v64 = s64["steps"] / (s64["kernel_ms"] * 1e-3)
         v32 = s32["steps"] / (s32["kernel_ms"] * 1e-3)
         fp64 = {"value": v64, "unit": "ion-steps/s", "sample_ions": m,
-                "sample": "the %d primaries of the first timed step%s" % (m, "" if m == n else " (first %d)" % m),
+                "sample": "%d primaries of the workload (the oracle's stored primaries 0..%d, seed %d)" % (m, m - 1, pseed),
                 "roofline": {"bound": "fp64", "achieved": a64, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
                              "frac": a64 / peaks["fp64_tflops"], "peak_source": "measured FP64 FMA stream (reed_peaks)"},
                 "launch": {"threads_per_track": s64["threads_per_track"], "ctas_per_sm": s64["ctas_per_sm"],
